@@ -1,0 +1,380 @@
+"""SpMM benchmark: GFLOP/s (2 nnz n / t) and HBM-roofline fraction on one GB300.
+
+Default workload: the 1M x 1M power-law CSR matrix (row lengths with density
+exponent 2, mean about 16, capped at 100,000, 1% empty rows) times row-major
+float32 B of widths n = 8, 32, 64, 128.  One step = C = A B for every width,
+each through the C ABI with the algorithm chosen by the Section 5.4 heuristic
+(``--alg`` overrides).  All inputs are synthetic and seeded (gen/).
+
+Timing: inputs resident in HBM; L2 is flushed (a write of twice its size)
+before every step, outside the events; each call is bracketed by CUDA events on
+the launching stream.  ``e2e`` times the same step through ``spmm_csr_host``
+(host buffers; H2D of A and B, D2H of C inside the timed region).
+``--impl reference`` times the FP64 CPU oracle on a bounded row sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------------------- args / env
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="power_law", choices=["power_law", "plain"])
+    p.add_argument("--n", type=int, nargs="*", default=None, help="dense widths (default 8 32 64 128)")
+    p.add_argument("--alg", default="auto", choices=["auto", "row_split", "merge"])
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown")
+    p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--tuning", default=None, help='JSON spmm_tuning_t fields, e.g. {"column_slabs": 2}')
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(name, ns):
+    if name == "plain":
+        a, B64 = gen.workload_plain()
+        ns = ns or [64]
+        Bs = {n: (B64 if n == 64 else gen.normal_matrix(a.k, n, gen.SEED_BASE + 1)) for n in ns}
+        label = "plain_4096x4096_16nnz"
+    else:
+        a = gen.workload_power_law()
+        ns = ns or [8, 32, 64, 128]
+        Bs = {n: gen.normal_matrix(a.k, n, gen.SEED_BASE + 2, stream=2 + n) for n in ns}
+        label = "power_law_1Mx1M_mean16_cap1e5"
+    return label, a, ns, Bs
+
+
+def compulsory_bytes(m, nnz, k, n, s_v=4, s_b=4, s_c=4):
+    """row_ptr + col_ind + vals + B (each row once) + C: the bytes any SpMM must move."""
+    return (m + 1) * 4 + nnz * (4 + s_v) + k * n * s_b + m * n * s_c
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, enabled=True):
+        self.enabled = enabled
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                              "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.reader = threading.Thread(target=self._read, daemon=True)
+                self.reader.start()
+            except (FileNotFoundError, OSError):
+                self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, gpu_index=None):
+        rows = []
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                idx, sm, smax = int(parts[0]), float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            if gpu_index is not None and idx != gpu_index:
+                continue
+            rows.append((sm, smax, parts[5:9]))
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def time_oracle_sample(a, ns, Bs, target_s=12.0, seed=0):
+    """FP64 oracle on a bounded, seeded sample of rows of the same workload.
+    Returns (GFLOP/s, seconds, rows sampled, threads)."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    lens = a.row_lengths()
+    rows = np.sort(rng.choice(a.m, size=min(a.m, 20_000), replace=False))
+    t0 = time.perf_counter()
+    for n in ns:
+        oracle.spmm_rows(rows, a.row_ptr, a.col_ind, a.vals, Bs[n])
+    t_probe = time.perf_counter() - t0
+    scale = max(1.0, target_s / max(t_probe, 1e-3))
+    rows = np.sort(rng.choice(a.m, size=int(min(a.m, len(rows) * scale)), replace=False))
+    flops, passes = 0.0, 0
+    t0 = time.perf_counter()
+    while True:  # whole passes over the sample until about target_s of CPU work
+        for n in ns:
+            oracle.spmm_rows(rows, a.row_ptr, a.col_ind, a.vals, Bs[n])
+        flops += sum(2.0 * float(lens[rows].sum()) * n for n in ns)
+        passes += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    t = time.perf_counter() - t0
+    return flops / t / 1e9, t, len(rows), oracle.num_threads(), passes
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    label, a, ns, Bs = make_workload(args.workload, args.n)
+    import oracle
+
+    vals = []
+    rng = np.random.default_rng(1)
+    lens = a.row_lengths()
+    per_step_rows = None
+    for step in range(args.warmup + args.steps):
+        if per_step_rows is None:
+            rows = np.sort(rng.choice(a.m, size=min(a.m, 20_000), replace=False))
+        else:
+            rows = np.sort(rng.choice(a.m, size=per_step_rows, replace=False))
+        t0 = time.perf_counter()
+        for n in ns:
+            oracle.spmm_rows(rows, a.row_ptr, a.col_ind, a.vals, Bs[n])
+        t = time.perf_counter() - t0
+        if per_step_rows is None:  # size later steps to about 8 s each
+            per_step_rows = int(min(a.m, len(rows) * max(1.0, 8.0 / max(t, 1e-3))))
+        if step >= args.warmup:
+            vals.append(sum(2.0 * float(lens[rows].sum()) * n for n in ns) / t / 1e9)
+    v = float(statistics.mean(vals))
+    line = {"impl": "reference", "metric": "SpMM GFLOP/s (2*nnz*n/t)", "value": v, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (gen/, seeded)",
+            "config": {"workload": label, "m": a.m, "k": a.k, "nnz": a.nnz, "n": ns},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step_rows} random rows of the {label} matrix per step, all n"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_1803_08601_gb300 as pkg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.build()
+    pkg.load()
+    label, a, ns, Bs = make_workload(args.workload, args.n)
+    m, k, nnz = a.m, a.k, a.nnz
+    stream = torch.cuda.current_stream()
+    d_rp = torch.from_numpy(a.row_ptr).to(dev)
+    d_ci = torch.from_numpy(a.col_ind).to(dev)
+    d_v = torch.from_numpy(a.vals).to(dev)
+    d_B = {n: torch.from_numpy(Bs[n]).to(dev) for n in ns}
+    d_C = {n: torch.empty((m, n), dtype=torch.float32, device=dev) for n in ns}
+    alg_of = {n: (pkg.spmm_select_alg(m, nnz, 0.0) if args.alg == "auto" else pkg.alg_code(args.alg)) for n in ns}
+    tuning_ws = json.loads(args.tuning) if args.tuning else None
+    ws_bytes = max(pkg.workspace_size(m, k, n, nnz, pkg.ALG_MERGE, tuning=tuning_ws) for n in ns)
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.float32, device=dev)
+
+    tuning = json.loads(args.tuning) if args.tuning else None
+
+    def one(n, alg):
+        pkg.spmm(d_rp, d_ci, d_v, d_B[n], alg=alg, out=d_C[n], nnz=nnz, workspace=ws, tuning=tuning)
+
+    def step(events=None):
+        for i, n in enumerate(ns):
+            if events is not None:
+                events[i][0].record(stream)
+            one(n, args.alg)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    per_call = {n: [] for n in ns}
+    launches0 = pkg.spmm_launch_count()
+    with ClockSampler(enabled=not args.no_clocks) as clk:
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in ns]
+            step(ev)
+            torch.cuda.synchronize()
+            for i, n in enumerate(ns):
+                per_call[n].append(ev[i][0].elapsed_time(ev[i][1]))
+        barrier()
+    launches = pkg.spmm_launch_count() - launches0
+    step_ms = [sum(per_call[n][s] for n in ns) for s in range(args.steps)]
+    local_ms = float(statistics.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([local_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        ms = local_ms
+    flops_step = sum(2.0 * nnz * n for n in ns)
+    value = world * flops_step / (ms * 1e-3) / 1e9
+
+    peak, peak_src = peaks()
+    # dominant kernel: the (alg, n) call with the largest share of the step; roofline of its family
+    comp = {n: compulsory_bytes(m, nnz, k, n) for n in ns}
+    mean_call = {n: float(statistics.mean(per_call[n])) for n in ns}
+    dom_alg = {pkg.ALG_ROW_SPLIT: "rowsplit_kernel", pkg.ALG_MERGE: "merge_kernel"}
+    fam = max({alg_of[n] for n in ns}, key=lambda al: sum(mean_call[n] for n in ns if alg_of[n] == al))
+    fam_ns = [n for n in ns if alg_of[n] == fam]
+    achieved = sum(comp[n] for n in fam_ns) / (sum(mean_call[n] for n in fam_ns) * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom_alg[fam], "peak_source": peak_src,
+                "algorithmic_bytes": "compulsory: (m+1)*4 + nnz*8 + k*n*4 + m*n*4 per call, summed over n",
+                "per_n": {str(n): {"ms": mean_call[n], "gb_s": comp[n] / (mean_call[n] * 1e-3) / 1e9,
+                                   "gflops": 2.0 * nnz * n / (mean_call[n] * 1e-3) / 1e9,
+                                   "alg": "merge" if alg_of[n] == pkg.ALG_MERGE else "row_split"} for n in ns}}
+
+    line = {"metric": "SpMM GFLOP/s (2*nnz*n/t)", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (gen/, seed 1805): power-law CSR, N(0,1) B",
+            "config": {"workload": label, "m": m, "k": k, "nnz": nnz, "n": ns, "alg": args.alg, "tuning": tuning,
+                       "replicas": world, "l2_flush": "2x L2 write before every step", "parallelism": "replicas"},
+            "roofline": roofline, "gpu_launches": int(launches)}
+    cs = clk.summary()
+    if cs:
+        line["clocks"] = cs
+
+    if rank == 0 and not args.no_extras:
+        line["breakdown"] = breakdown(pkg, torch, one, ns, nnz, comp, args.steps, flush, stream)
+        line["e2e"] = e2e(pkg, torch, a, ns, Bs, args)
+        if world == 1:
+            g, t, nrows, thr, passes = time_oracle_sample(a, ns, Bs)
+            line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
+                                    "sample": f"{passes} pass(es) over {nrows} seeded random rows of the {label} "
+                                              f"matrix, all n, {t:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def breakdown(pkg, torch, one, ns, nnz, comp, steps, flush, stream):
+    """GFLOP/s and compulsory GB/s of each algorithm family at every n (same timing rules)."""
+    out = {}
+    for alg in ("row_split", "merge"):
+        out[alg] = {}
+        for n in ns:
+            for _ in range(2):
+                one(n, alg)
+            ts = []
+            for _ in range(max(3, steps // 2)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one(n, alg)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t = statistics.median(ts)
+            out[alg][str(n)] = {"ms": t, "gflops": 2.0 * nnz * n / (t * 1e-3) / 1e9,
+                                "gb_s": comp[n] / (t * 1e-3) / 1e9}
+    return out
+
+
+def e2e(pkg, torch, a, ns, Bs, args):
+    """The step through spmm_csr_host: pinned host A, B in; host C out; copies timed."""
+    rp = torch.from_numpy(a.row_ptr).pin_memory()
+    ci = torch.from_numpy(a.col_ind).pin_memory()
+    v = torch.from_numpy(a.vals).pin_memory()
+    hB = {n: torch.from_numpy(Bs[n]).pin_memory() for n in ns}
+    hC = {n: torch.empty((a.m, n), dtype=torch.float32).pin_memory() for n in ns}
+    h2d = sum((a.m + 1) * 4 + a.nnz * 8 + a.k * n * 4 for n in ns)
+    d2h = sum(a.m * n * 4 for n in ns)
+    for n in ns:
+        pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg)
+    torch.cuda.synchronize()
+    reps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for n in ns:
+            pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg)
+    t = (time.perf_counter() - t0) / reps
+    flops = sum(2.0 * a.nnz * n for n in ns)
+    return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": t * 1e3, "api": "spmm_csr_host"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

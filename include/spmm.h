@@ -1,0 +1,171 @@
+/*
+ * spmm.h - C ABI of the GB300 (sm_103a) CSR x dense SpMM library.
+ *
+ * Method: "Design Principles for Sparse Matrix Multiplication on the GPU"
+ * (Yang, Buluc, Owens, arXiv 1803.08601).  Given an m x k sparse matrix A in
+ * CSR form and a k x n dense row-major matrix B, the library computes the
+ * m x n dense row-major product C = A B (Section 1), with the paper's two
+ * algorithm families and its selection heuristic:
+ *   - row split (Section 4.1, Fig. 3): a group of lanes per row of A, lanes
+ *     striding the columns of B with 128-bit coalesced loads, column indices
+ *     and values broadcast between lanes by warp shuffles;
+ *   - merge based (Section 4.2, Algorithm 1): a merge-path partition of
+ *     rows + nonzeros into equal tiles, a compute pass per tile, and a
+ *     carry-out fix-up for rows that cross tiles;
+ *   - the Section 5.4 heuristic: merge based when nnz / m < 9.35.
+ *
+ * Conventions shared by every entry point unless stated otherwise:
+ *   - Array arguments are DEVICE pointers owned by the caller; the library
+ *     keeps no reference after the call returns.
+ *   - Indices are 0-based int32.  row_ptr has m + 1 entries, row_ptr[0] = 0,
+ *     non-decreasing; 0 <= col_ind[p] < k.  Column indices inside a row need
+ *     not be sorted; repeated indices are summed.  Out-of-range indices are a
+ *     precondition violation (not checked; the result is undefined).
+ *   - Dense matrices are row-major with leading dimension (row stride, in
+ *     elements) ldb >= n, ldc >= n.
+ *   - C is overwritten (beta = 0); rows of A without nonzeros give zero rows.
+ *   - Accumulation is float32 in every precision form.  16-bit outputs are
+ *     rounded to nearest even once per element.
+ *   - `stream` is a cudaStream_t handle (NULL = the legacy default stream).
+ *     Work is enqueued asynchronously; a return of SPMM_OK means the launch
+ *     was accepted, not that the kernels finished.  Errors found on the
+ *     device (bounded waits that ran out) are written to the optional device
+ *     status word `d_status` as SPMM_ERR_TIMEOUT.
+ *   - No entry point aborts, throws, or falls back to the CPU.
+ */
+#ifndef SPMM_GB300_H
+#define SPMM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMM_ALG_AUTO = 0,      /* Section 5.4 heuristic on the mean row length     */
+    SPMM_ALG_ROW_SPLIT = 1, /* Section 4.1, Algorithm I                         */
+    SPMM_ALG_MERGE = 2      /* Section 4.2, Algorithm II (Algorithm 1)          */
+} spmm_alg_t;
+
+typedef enum {
+    SPMM_F32 = 0,  /* IEEE binary32            */
+    SPMM_BF16 = 1, /* bfloat16 (8-bit exponent) */
+    SPMM_F16 = 2   /* IEEE binary16            */
+} spmm_dtype_t;
+
+typedef enum {
+    SPMM_OK = 0,
+    SPMM_ERR_INVALID_VALUE = 1, /* a size, pointer, stride or enum is invalid   */
+    SPMM_ERR_ALLOC = 2,         /* device memory could not be obtained          */
+    SPMM_ERR_LAUNCH = 3,        /* a kernel launch was rejected                 */
+    SPMM_ERR_BAD_CSR = 4,       /* reserved for CSR structure checks            */
+    SPMM_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out           */
+    SPMM_ERR_UNSUPPORTED = 6,   /* dtype combination not provided               */
+    SPMM_ERR_CUDA = 7,          /* another CUDA runtime error                   */
+    SPMM_ERR_WORKSPACE = 8      /* workspace pointer NULL or too small          */
+} spmm_status_t;
+
+/* Optional launch shape.  Zero in a field selects the library's choice. */
+typedef struct {
+    int lanes_per_row;       /* lanes that share one row of A: 1, 2, 4, 8, 16 or 32        */
+    int column_slabs;        /* split the n columns into this many slabs (grid y); B's
+                                rows are then gathered one slab at a time, which keeps
+                                a slab of B resident in L2                              */
+    int items_per_subwarp;   /* merge based: merge-path items (rows + nonzeros) per
+                                lane group; a tile holds 256 / lanes_per_row groups     */
+    double merge_threshold;  /* heuristic threshold on nnz / m; <= 0 selects 9.35       */
+} spmm_tuning_t;
+
+/* Human-readable name of a status code (static storage). */
+const char *spmm_status_string(int status);
+
+/* Library ABI version (major * 100 + minor). */
+int spmm_version(void);
+
+/* Number of kernels this library has launched in this process (all devices).
+   Host-side counter, incremented at every successful launch. */
+long long spmm_launch_count(void);
+
+/*
+ * Section 5.4 heuristic.  d = nnz / m is the mean row length of A; returns
+ * SPMM_ALG_MERGE when d < threshold and SPMM_ALG_ROW_SPLIT otherwise
+ * (threshold <= 0 selects the paper's 9.35).  m == 0 returns row split.
+ * Pure host function.
+ */
+int spmm_select_alg(int m, long long nnz, double threshold);
+
+/*
+ * C = A B in float32 (vals, B, C all float32), the signature of the paper's
+ * problem statement (Section 1).  alg is a spmm_alg_t.  For SPMM_ALG_AUTO the
+ * heuristic needs nnz = row_ptr[m], which this call reads back from the device
+ * (a 4-byte copy that synchronises `stream`); use spmm_csr_ex with a host nnz
+ * to avoid it.  Merge-based launches take their workspace from a
+ * stream-ordered allocation (cudaMallocAsync) released on the same stream.
+ */
+int spmm_csr(int m, int k, int n, const int *row_ptr, const int *col_ind, const float *vals,
+             const float *B, long long ldb, float *C, long long ldc, int alg, void *stream);
+
+/*
+ * Full form.  nnz is the host copy of row_ptr[m] (pass -1 to have it read
+ * back, which synchronises `stream`).  vals_type / b_type / c_type are
+ * spmm_dtype_t values; the supported combinations (vals, B, C) are
+ * (f32,f32,f32), (bf16,bf16,bf16), (bf16,bf16,f32), (bf16,f16,f16),
+ * (bf16,f16,f32), (f16,f16,f16) and (f16,f16,f32); others return
+ * SPMM_ERR_UNSUPPORTED.  `tuning` may be NULL.
+ * workspace: device memory of at least spmm_csr_workspace_size(...) bytes for
+ * the merge-based algorithm (row split needs none); NULL with
+ * workspace_bytes == 0 makes the call allocate it stream-ordered itself.
+ * The workspace must not be used by another call that may run concurrently.
+ * d_status: optional device int; a bounded wait that runs out stores
+ * SPMM_ERR_TIMEOUT there (the caller clears it).
+ */
+int spmm_csr_ex(int m, int k, int n, long long nnz, const int *row_ptr, const int *col_ind,
+                const void *vals, int vals_type, const void *B, int b_type, long long ldb, void *C,
+                int c_type, long long ldc, int alg, const spmm_tuning_t *tuning, void *workspace,
+                size_t workspace_bytes, int *d_status, void *stream);
+
+/*
+ * Bytes of workspace spmm_csr_ex needs for these sizes.  0 for row split.
+ * alg SPMM_ALG_AUTO is resolved with the heuristic first.  Returns 0 for
+ * invalid arguments.
+ */
+size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int b_type,
+                               const spmm_tuning_t *tuning);
+
+/*
+ * Merge-path partition (Section 4.2, PARTITIONSPMM of Algorithm 1; Section 4
+ * item 2(b), Fig. 2(c)) on its own.  For t = 0 .. num_tiles, limits[2t] and
+ * limits[2t + 1] receive (rows consumed, nonzeros consumed) where the merge of
+ * the row end offsets row_ptr[1..m] with the nonzero indices 0..nnz-1 (row end
+ * first on ties) crosses diagonal min(t * items_per_tile, m + nnz).
+ * limits: device int array of 2 * (num_tiles + 1) entries.
+ */
+int spmm_merge_partition(int m, long long nnz, const int *row_ptr, int items_per_tile, int num_tiles,
+                         int *limits, void *stream);
+
+/*
+ * C = A B with every array in HOST memory: the call copies A and B to the
+ * device, computes, copies C back and synchronises `stream` before it returns.
+ * Types and alg as in spmm_csr_ex; nnz is read from the host row_ptr[m].
+ * Device buffers are obtained stream-ordered and released before return.
+ * Pinned (page-locked) host buffers make the copies asynchronous DMA.
+ */
+int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
+                  int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,
+                  long long ldc, int alg, const spmm_tuning_t *tuning, void *stream);
+
+/*
+ * Self-test of the bounded device-side wait used by the merge kernel's
+ * shared-memory staging: one CTA waits on an mbarrier phase that nothing
+ * completes, for at most limit_ns nanoseconds of device time (clamped to
+ * [1e3, 2e9]), then stores SPMM_ERR_TIMEOUT to *d_status and returns.  The
+ * context stays usable.  Not part of the paper; used by the failure tests.
+ */
+int spmm_debug_bounded_wait(int *d_status, long long limit_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMM_GB300_H */

@@ -1,0 +1,248 @@
+"""GB300 (sm_103a) CSR x dense SpMM: Python binding of ``libspmm_gb300.so``.
+
+The C ABI (``include/spmm.h``) is the boundary; this module only marshals
+arguments to it.  Every step of the computation runs in the library's CUDA
+kernels: there is no CPU path, and calls fail loudly when the library or a
+GPU is missing.
+
+Two layers:
+
+* the C entry points under their C names (``spmm_csr``, ``spmm_csr_ex``,
+  ``spmm_csr_workspace_size``, ``spmm_select_alg``, ``spmm_merge_partition``,
+  ``spmm_csr_host``, ...), taking integers for pointers and streams exactly as
+  the C functions do;
+* tensor helpers (``spmm``, ``merge_partition``, ``spmm_host``) that take
+  torch CUDA tensors, use torch only for device memory and the current stream,
+  and raise ``SpMMError`` on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE = 0, 1, 2
+F32, BF16, F16 = 0, 1, 2
+OK = 0
+ERR_INVALID_VALUE, ERR_ALLOC, ERR_LAUNCH, ERR_BAD_CSR, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE = range(1, 9)
+PAPER_THRESHOLD = 9.35  # Section 5.4
+
+_ALG_NAMES = {"auto": ALG_AUTO, "row_split": ALG_ROW_SPLIT, "rowsplit": ALG_ROW_SPLIT, "merge": ALG_MERGE}
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspmm_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class SpMMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+class SpmmTuning(ctypes.Structure):
+    """Mirror of spmm_tuning_t (zero fields = library's choice)."""
+
+    _fields_ = [("lanes_per_row", ctypes.c_int), ("column_slabs", ctypes.c_int),
+                ("items_per_subwarp", ctypes.c_int), ("merge_threshold", ctypes.c_double)]
+
+
+_i, _ll, _vp, _sz, _d = ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double
+_TP = ctypes.POINTER(SpmmTuning)
+_SIGNATURES = {
+    "spmm_status_string": ([_i], ctypes.c_char_p),
+    "spmm_version": ([], _i),
+    "spmm_launch_count": ([], _ll),
+    "spmm_select_alg": ([_i, _ll, _d], _i),
+    "spmm_csr": ([_i, _i, _i, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _vp], _i),
+    "spmm_csr_ex": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _sz, _vp, _vp], _i),
+    "spmm_csr_workspace_size": ([_i, _i, _i, _ll, _i, _i, _TP], _sz),
+    "spmm_merge_partition": ([_i, _ll, _vp, _i, _i, _vp, _vp], _i),
+    "spmm_csr_host": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
+    "spmm_debug_bounded_wait": ([_vp, _ll, _vp], _i),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    from . import _build
+
+    return _build.build(force=force)
+
+
+def load():
+    """Load the library (it must have been built; no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1803_08601_gb300.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+# ----------------------------------------------------------------------------- C entry points
+
+def spmm_status_string(status: int) -> str:
+    return load().spmm_status_string(status).decode()
+
+
+status_string = spmm_status_string
+
+
+def spmm_version() -> int:
+    return load().spmm_version()
+
+
+def spmm_launch_count() -> int:
+    return load().spmm_launch_count()
+
+
+def spmm_select_alg(m: int, nnz: int, threshold: float = 0.0) -> int:
+    return load().spmm_select_alg(m, nnz, threshold)
+
+
+def spmm_csr(m, k, n, row_ptr, col_ind, vals, B, ldb, C, ldc, alg, stream) -> int:
+    return load().spmm_csr(m, k, n, row_ptr, col_ind, vals, B, ldb, C, ldc, alg, stream)
+
+
+def spmm_csr_ex(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                workspace, workspace_bytes, d_status, stream) -> int:
+    return load().spmm_csr_ex(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg,
+                              _tuning_ptr(tuning), workspace, workspace_bytes, d_status, stream)
+
+
+def spmm_csr_workspace_size(m, k, n, nnz, alg, b_type, tuning=None) -> int:
+    return load().spmm_csr_workspace_size(m, k, n, nnz, alg, b_type, _tuning_ptr(tuning))
+
+
+def spmm_merge_partition(m, nnz, row_ptr, items_per_tile, num_tiles, limits, stream) -> int:
+    return load().spmm_merge_partition(m, nnz, row_ptr, items_per_tile, num_tiles, limits, stream)
+
+
+def spmm_csr_host(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                  stream) -> int:
+    return load().spmm_csr_host(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg,
+                                _tuning_ptr(tuning), stream)
+
+
+def spmm_debug_bounded_wait(d_status, limit_ns, stream) -> int:
+    return load().spmm_debug_bounded_wait(d_status, limit_ns, stream)
+
+
+def _tuning_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, dict):
+        t = SpmmTuning(**t)
+    return ctypes.pointer(t)
+
+
+# ----------------------------------------------------------------------------- tensor helpers
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def dtype_code(dt) -> int:
+    torch = _torch()
+    m = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+    if dt not in m:
+        raise TypeError(f"unsupported dtype {dt}")
+    return m[dt]
+
+
+def alg_code(alg) -> int:
+    return _ALG_NAMES[alg] if isinstance(alg, str) else int(alg)
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise SpMMError(status, where)
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must live on a CUDA device (no CPU path exists)")
+
+
+def spmm(row_ptr, col_ind, vals, B, alg="auto", out=None, out_dtype=None, nnz=None, tuning=None, workspace=None,
+         status=None, stream=None):
+    """C = A @ B for a CSR A (row_ptr int32 [m+1], col_ind int32 [nnz], vals) and a
+    row-major B [k, n] (row stride B.stride(0)).  Returns C [m, n] (or fills ``out``).
+
+    ``nnz`` (host int) avoids the device read of row_ptr[m] that AUTO needs.
+    ``workspace``: optional uint8 CUDA tensor for the merge-based path.
+    ``status``: optional int32 CUDA tensor of one element receiving device-side errors.
+    """
+    torch = _torch()
+    _require_cuda(row_ptr, col_ind, vals, B, out)
+    if row_ptr.dtype != torch.int32 or col_ind.dtype != torch.int32:
+        raise TypeError("row_ptr and col_ind must be int32")
+    if B.dim() != 2 or B.stride(1) != 1:
+        raise ValueError("B must be a row-major 2-D tensor")
+    m = row_ptr.numel() - 1
+    k, n = B.shape
+    if out is None:
+        out = torch.empty((m, n), dtype=out_dtype or B.dtype, device=B.device)
+    if out.dim() != 2 or out.shape != (m, n) or out.stride(1) != 1:
+        raise ValueError("out must be a row-major [m, n] tensor")
+    ws_ptr, ws_bytes = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None else (None, 0)
+    st = spmm_csr_ex(m, k, n, -1 if nnz is None else int(nnz), row_ptr.data_ptr(), col_ind.data_ptr(),
+                     vals.data_ptr(), dtype_code(vals.dtype), B.data_ptr(), dtype_code(B.dtype), B.stride(0),
+                     out.data_ptr(), dtype_code(out.dtype), out.stride(0), alg_code(alg), tuning, ws_ptr, ws_bytes,
+                     status.data_ptr() if status is not None else None, _stream_handle(stream))
+    _check(st, "spmm_csr_ex")
+    return out
+
+
+def merge_partition(row_ptr, items_per_tile: int, nnz: int | None = None, stream=None):
+    """Merge-path split points of Section 4.2 as an int32 CUDA tensor [tiles + 1, 2]."""
+    torch = _torch()
+    _require_cuda(row_ptr)
+    m = row_ptr.numel() - 1
+    if nnz is None:
+        nnz = int(row_ptr[-1].item()) if m > 0 else 0
+    tiles = (m + nnz + items_per_tile - 1) // items_per_tile
+    lim = torch.empty((tiles + 1, 2), dtype=torch.int32, device=row_ptr.device)
+    _check(spmm_merge_partition(m, nnz, row_ptr.data_ptr(), items_per_tile, tiles, lim.data_ptr(),
+                                _stream_handle(stream)), "spmm_merge_partition")
+    return lim
+
+
+def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None):
+    """C = A @ B with every operand in host memory (CPU tensors, ideally pinned):
+    the library copies to the device, computes, copies back and synchronises."""
+    for t in (row_ptr, col_ind, vals, B, C):
+        if t.is_cuda:
+            raise ValueError("spmm_host takes host tensors")
+    m = row_ptr.numel() - 1
+    k, n = B.shape
+    st = spmm_csr_host(m, k, n, row_ptr.data_ptr(), col_ind.data_ptr(), vals.data_ptr(), dtype_code(vals.dtype),
+                       B.data_ptr(), dtype_code(B.dtype), B.stride(0), C.data_ptr(), dtype_code(C.dtype), C.stride(0),
+                       alg_code(alg), tuning, _stream_handle(stream))
+    _check(st, "spmm_csr_host")
+    return C
+
+
+def workspace_size(m, k, n, nnz, alg="auto", b_dtype=None, tuning=None) -> int:
+    torch = _torch()
+    return spmm_csr_workspace_size(m, k, n, nnz, alg_code(alg), dtype_code(b_dtype or torch.float32), tuning)

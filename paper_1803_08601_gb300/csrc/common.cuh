@@ -1,0 +1,225 @@
+// Device-side building blocks shared by the SpMM kernels: element types and
+// 128-bit vector loads/stores, float32 accumulation helpers, and the bulk-copy
+// (TMA) / mbarrier primitives with bounded waits.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spmm.h"
+
+namespace spmm {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kThreads = 256;  // threads per CTA of every SpMM kernel
+constexpr int kUnroll = 8;     // gathers of B in flight per lane
+
+// ------------------------------------------------------------------ element types
+
+template <typename T> struct Elem;
+template <> struct Elem<float> {
+    static constexpr int kVec = 4;  // elements per 16-byte vector
+    __device__ __forceinline__ static float to_f(float x) { return x; }
+    __device__ __forceinline__ static float from_f(float x) { return x; }
+};
+template <> struct Elem<__nv_bfloat16> {
+    static constexpr int kVec = 8;
+    __device__ __forceinline__ static float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+    __device__ __forceinline__ static __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+    __device__ __forceinline__ static __nv_bfloat16 from_bits(uint16_t b) { return __ushort_as_bfloat16(b); }
+    __device__ __forceinline__ static uint16_t to_bits(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
+};
+template <> struct Elem<__half> {
+    static constexpr int kVec = 8;
+    __device__ __forceinline__ static float to_f(__half x) { return __half2float(x); }
+    __device__ __forceinline__ static __half from_f(float x) { return __float2half_rn(x); }
+    __device__ __forceinline__ static __half from_bits(uint16_t b) { return __ushort_as_half(b); }
+    __device__ __forceinline__ static uint16_t to_bits(__half x) { return __half_as_ushort(x); }
+};
+
+// Read-only load of one value as float.
+template <typename T>
+__device__ __forceinline__ float load_f(const T* p) {
+    return Elem<T>::to_f(__ldg(p));
+}
+
+// Load VEC consecutive elements starting at p (VEC == 1 or the 16-byte width
+// of T, in which case p is 16-byte aligned) and widen them to float.
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T* p, float (&out)[VEC]) {
+    if constexpr (VEC == 1) {
+        out[0] = load_f(p);
+    } else if constexpr (sizeof(T) == 4) {
+        static_assert(VEC == 4, "float vectors are 4 wide");
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else {
+        static_assert(VEC == 8, "16-bit vectors are 8 wide");
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            out[2 * i] = Elem<T>::to_f(Elem<T>::from_bits((uint16_t)(w[i] & 0xffffu)));
+            out[2 * i + 1] = Elem<T>::to_f(Elem<T>::from_bits((uint16_t)(w[i] >> 16)));
+        }
+    }
+}
+
+// Raw (not yet widened) storage of VEC elements of T as one load brings them
+// in: the gathers of a batch are issued into these, and widened only when they
+// are accumulated, so a batch of 16-bit rows costs 4 registers per gather.
+template <typename T, int VEC> struct Raw;
+template <typename T> struct Raw<T, 1> { T v; };
+template <> struct Raw<float, 4> { float4 v; };
+template <> struct Raw<__nv_bfloat16, 8> { uint4 v; };
+template <> struct Raw<__half, 8> { uint4 v; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ Raw<T, VEC> load_raw(const T* p) {
+    Raw<T, VEC> r;
+    if constexpr (VEC == 1) r.v = __ldg(p);
+    else if constexpr (sizeof(T) == 4) r.v = __ldg(reinterpret_cast<const float4*>(p));
+    else r.v = __ldg(reinterpret_cast<const uint4*>(p));
+    return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ Raw<T, VEC> zero_raw() {
+    Raw<T, VEC> r;
+    if constexpr (VEC == 1) r.v = Elem<T>::from_f(0.0f);
+    else if constexpr (sizeof(T) == 4) r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+    else r.v = make_uint4(0u, 0u, 0u, 0u);
+    return r;
+}
+
+// acc[e] += a * element e of r, in float32 (fused multiply-add).
+template <typename T, int VEC>
+__device__ __forceinline__ void fma_raw(float (&acc)[VEC], float a, const Raw<T, VEC>& r) {
+    if constexpr (VEC == 1) {
+        acc[0] = fmaf(a, Elem<T>::to_f(r.v), acc[0]);
+    } else if constexpr (sizeof(T) == 4) {
+        acc[0] = fmaf(a, r.v.x, acc[0]);
+        acc[1] = fmaf(a, r.v.y, acc[1]);
+        acc[2] = fmaf(a, r.v.z, acc[2]);
+        acc[3] = fmaf(a, r.v.w, acc[3]);
+    } else {
+        const uint32_t w[4] = {r.v.x, r.v.y, r.v.z, r.v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[2 * i] = fmaf(a, Elem<T>::to_f(Elem<T>::from_bits((uint16_t)(w[i] & 0xffffu))), acc[2 * i]);
+            acc[2 * i + 1] = fmaf(a, Elem<T>::to_f(Elem<T>::from_bits((uint16_t)(w[i] >> 16))), acc[2 * i + 1]);
+        }
+    }
+}
+
+// Store VEC floats as TC at p (p aligned to VEC * sizeof(TC) when VEC > 1).
+template <typename TC, int VEC>
+__device__ __forceinline__ void store_vec(TC* p, const float (&v)[VEC]) {
+    if constexpr (VEC == 1) {
+        p[0] = Elem<TC>::from_f(v[0]);
+    } else if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+        for (int i = 0; i < VEC; i += 4)
+            *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+        // 16-bit output: pack pairs, write 8 or 16 bytes at a time
+        uint32_t w[VEC / 2];
+#pragma unroll
+        for (int i = 0; i < VEC / 2; ++i) {
+            const uint32_t l = Elem<TC>::to_bits(Elem<TC>::from_f(v[2 * i]));
+            const uint32_t h = Elem<TC>::to_bits(Elem<TC>::from_f(v[2 * i + 1]));
+            w[i] = l | (h << 16);
+        }
+        if constexpr (VEC == 8) {
+            *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            static_assert(VEC == 4, "unexpected vector width");
+            *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ timing / status
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void report(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ mbarrier + bulk copy
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait until phase `parity` of the barrier completes, for at most limit_ns of
+// device time.  Returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared (TMA engine, no multicast), completing
+// `bytes` transactions on `bar`.  dst and src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Round an element index down / up to a 16-byte boundary of T.
+template <typename T>
+__host__ __device__ __forceinline__ long long align_down16(long long i) {
+    constexpr long long g = 16 / (long long)sizeof(T);
+    return i - (i % g + g) % g;
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long align_up16(long long i) {
+    constexpr long long g = 16 / (long long)sizeof(T);
+    return align_down16<T>(i + g - 1);
+}
+
+}  // namespace spmm

@@ -1,0 +1,4 @@
+// Instantiation of the SpMM launchers for (vals, B, C) = (__nv_bfloat16, __nv_bfloat16, float).
+#include "launch.cuh"
+
+SPMM_DEFINE_LAUNCHERS(launchers_bf16_bf16_f32, __nv_bfloat16, __nv_bfloat16, float)

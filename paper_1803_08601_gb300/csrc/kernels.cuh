@@ -1,0 +1,524 @@
+// CSR x dense SpMM kernels for sm_103a: row split (Section 4.1), merge-path
+// partition / compute / carry-out fix-up (Section 4.2, Algorithm 1).
+//
+// Both families share the memory access pattern the paper identifies as the
+// key to SpMM performance (Section 4.1, "Memory access pattern"; Fig. 3(c)):
+// a group of W lanes owns one row of A at a time, and each lane owns VEC
+// consecutive columns of B and C, so that every gathered row of B and every
+// stored row of C is read or written with W coalesced 16-byte accesses.  The
+// column index and value of a nonzero are loaded by one lane and broadcast to
+// the other lanes of its group with warp shuffles (Section 4.1, "Shared
+// memory": shuffle broadcast instead of shared memory).  A batch of kUnroll
+// gathers is issued before any of them is accumulated (instruction-level
+// parallelism, Section 3.1).
+//
+// Column slabs: gridDim.y (row split) or the slab part of the work index
+// (merge) selects which W * VEC columns a CTA covers, so n of any size is
+// handled, and a narrower slab keeps the slab of B that is being gathered
+// resident in L2.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmm {
+
+struct RowSplitArgs {
+    int m, n;
+    const int* row_ptr;
+    const int* col_ind;
+    const void* vals;
+    const void* B;
+    long long ldb;
+    void* C;
+    long long ldc;
+};
+
+// ============================================================================ row split
+//
+// Algorithm I (Section 4.1, Fig. 3).  Sub-warp of W lanes per row; the warp's
+// 32 / W rows are processed together.  Loop trip counts are made uniform over
+// the warp (the longest row of the warp sets them) so that the shuffles always
+// run with the full mask; lanes past the end of their row load nothing
+// (Section 4.1 passes a dummy column index there; predication does the same
+// without the load).
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
+    constexpr int U = kUnroll;
+    constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
+    constexpr int BS = W * CV;               // nonzeros per batch
+    constexpr int G = BS / U;                // groups of U gathers per batch
+    constexpr int RPW = 32 / W;              // rows per warp
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (W - 1);
+    const long long row = (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + lane / W;
+    const long long col0 = (long long)blockIdx.y * (W * VEC) + (long long)sl * VEC;
+    const bool col_ok = col0 < a.n;
+    const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
+    const TB* __restrict__ B = static_cast<const TB*>(a.B);
+
+    int rs = 0, re = 0;
+    if (row < a.m) {
+        rs = __ldg(a.row_ptr + row);
+        re = __ldg(a.row_ptr + row + 1);
+    }
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+
+    const int nb = (re - rs + BS - 1) / BS;
+    const int nb_max = __reduce_max_sync(kFullMask, nb);
+    for (int b = 0; b < nb_max; ++b) {
+        const int base = rs + b * BS;
+        const int cnt = re - base;  // nonzeros left in this row (may be <= 0)
+        int mc[CV];
+        float mv[CV];
+#pragma unroll
+        for (int c = 0; c < CV; ++c) {
+            const int p = base + c * W + sl;
+            const bool ok = p < re;
+            mc[c] = ok ? __ldg(a.col_ind + p) : 0;
+            mv[c] = ok ? load_f(vals + p) : 0.0f;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g > 0 && __all_sync(kFullMask, g * U >= cnt)) break;
+            Raw<TB, VEC> bv[U];
+            float vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = g * U + u;  // nonzero j of the batch sits in lane j % W, slot j / W
+                const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
+                vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+        }
+    }
+    if (row < a.m && col_ok) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc);
+}
+
+// ============================================================================ merge path
+//
+// Algorithm II (Section 4.2, Algorithm 1).  The path that merges the row end
+// offsets row_ptr[1..m] with the nonzero indices 0..nnz-1 (Section 4 item
+// 2(b), Fig. 2(c)) is cut into tiles of equal length (rows + nonzeros): every
+// CTA-sized tile carries the same amount of work whatever the row lengths.
+//
+struct MergeArgs {
+    int m, n;
+    long long nnz;
+    const int* row_ptr;
+    const int* col_ind;
+    const void* vals;
+    const void* B;
+    long long ldb;
+    void* C;
+    long long ldc;
+    const int2* limits;  // [num_tiles + 1] tile boundary coordinates
+    int num_tiles;
+    int slabs;            // column slabs; work item = slab * num_tiles + tile
+    int ips;              // merge-path items per lane group
+    float* carry;         // [num_tiles][n] partial sum of the row a tile leaves unfinished
+    float* head;          // [num_tiles][n] partial sum of the row a tile finishes but did not start
+    int* carry_row;       // [num_tiles] that row, or -1
+    int* head_row;        // [num_tiles] that row, or -1
+    int* status;          // optional device status word
+    int use_tma;          // 1: 1-D bulk copies into shared memory, 0: cooperative loads
+    unsigned long long wait_ns;  // limit of every mbarrier wait
+};
+
+// Shared-memory plan of the merge kernel: two staging buffers (row_ptr window,
+// col_ind window, vals window), then the per-lane-group first-row and carry
+// partial sums used to combine rows that cross lane groups inside a tile.
+template <typename TV, int VEC, int W>
+struct MergeSmem {
+    static constexpr int S = kThreads / W;  // lane groups per CTA
+    static constexpr int SW = W * VEC;      // columns per slab
+    static __host__ __device__ int ipt(int ips) { return S * ips; }
+    static __host__ __device__ int rp_cap(int ips) { return ipt(ips) + 8; }
+    static __host__ __device__ int col_cap(int ips) { return ipt(ips) + 8; }
+    static __host__ __device__ int val_cap(int ips) { return ipt(ips) + 16; }
+    static __host__ __device__ size_t r16(size_t b) { return (b + 15) & ~size_t(15); }
+    static __host__ __device__ size_t buf_bytes(int ips) {
+        return r16(rp_cap(ips) * 4) + r16(col_cap(ips) * 4) + r16(val_cap(ips) * sizeof(TV));
+    }
+    static constexpr size_t kHeader = 128;  // 2 mbarriers + 2 x (int4 coords + int4 offsets)
+    static __host__ __device__ size_t groups_offset(int ips) { return kHeader + 2 * buf_bytes(ips); }
+    static __host__ __device__ size_t total(int ips) {
+        return groups_offset(ips) + 2 * (size_t)S * SW * 4 + 2 * (size_t)S * 4;
+    }
+};
+
+struct Window {
+    long long a, e;  // bulk-copied element range [a, e), 16-byte aligned ends
+};
+
+// Elements [lo, hi) of an array of `len` elements: the bulk copy covers the
+// 16-byte-aligned span [a, e) around them that stays inside the array; only
+// the array's last partial 16 bytes (when the window reaches them) are loaded
+// with plain loads.
+template <typename T>
+__device__ __forceinline__ Window make_window(long long lo, long long hi, long long len) {
+    Window w;
+    w.a = align_down16<T>(lo);
+    long long e = align_up16<T>(hi);
+    const long long lim = align_down16<T>(len);
+    if (e > lim) e = lim;
+    w.e = e > w.a ? e : w.a;
+    return w;
+}
+
+template <typename TV, int VEC, int W>
+struct MergeView {
+    using L = MergeSmem<TV, VEC, W>;
+    unsigned char* base;
+    int ips;
+    __device__ uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base) + b; }
+    __device__ int4* coords(int b) const { return reinterpret_cast<int4*>(base + 16) + 2 * b; }
+    __device__ int4* offs(int b) const { return reinterpret_cast<int4*>(base + 16) + 2 * b + 1; }
+    __device__ unsigned char* buf(int b) const { return base + L::kHeader + b * L::buf_bytes(ips); }
+    __device__ int* rp(int b) const { return reinterpret_cast<int*>(buf(b)); }
+    __device__ int* col(int b) const { return reinterpret_cast<int*>(buf(b) + L::r16(L::rp_cap(ips) * 4)); }
+    __device__ TV* val(int b) const {
+        return reinterpret_cast<TV*>(buf(b) + L::r16(L::rp_cap(ips) * 4) + L::r16(L::col_cap(ips) * 4));
+    }
+    __device__ float* first(int s) const {
+        return reinterpret_cast<float*>(base + L::groups_offset(ips)) + (size_t)s * L::SW;
+    }
+    __device__ float* carry(int s) const {
+        return reinterpret_cast<float*>(base + L::groups_offset(ips)) + (size_t)(L::S + s) * L::SW;
+    }
+    __device__ int* first_row() const {
+        return reinterpret_cast<int*>(base + L::groups_offset(ips) + 2 * (size_t)L::S * L::SW * 4);
+    }
+    __device__ int* carry_row() const { return first_row() + L::S; }
+};
+
+// GLOBALTOSHARED of Algorithm 1: bring a tile's row_ptr window [r0, r1] and its
+// col_ind / vals window [z0, z1) into staging buffer b.  Run by warp 0 only.
+// With TMA, lane 0 announces the byte count on the buffer's mbarrier and
+// issues up to three 1-D bulk copies; the array tails (at most 15 bytes each)
+// are loaded by the other lanes.  Without TMA the caller loads cooperatively.
+template <typename TV, int VEC, int W>
+__device__ __forceinline__ void merge_stage(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
+    const int lane = threadIdx.x & 31;
+    const int tile = item % a.num_tiles;
+    int2 l0 = make_int2(0, 0), l1 = make_int2(0, 0);
+    if (lane == 0) {
+        l0 = a.limits[tile];
+        l1 = a.limits[tile + 1];
+    }
+    l0.x = __shfl_sync(kFullMask, l0.x, 0);
+    l0.y = __shfl_sync(kFullMask, l0.y, 0);
+    l1.x = __shfl_sync(kFullMask, l1.x, 0);
+    l1.y = __shfl_sync(kFullMask, l1.y, 0);
+    const int r0 = l0.x, z0 = l0.y, r1 = l1.x, z1 = l1.y;
+    const Window wr = make_window<int>(r0, (long long)r1 + 1, (long long)a.m + 1);
+    const Window wc = make_window<int>(z0, z1, a.nnz);
+    const Window wv = make_window<TV>(z0, z1, a.nnz);
+    int* srp = v.rp(b);
+    int* scol = v.col(b);
+    TV* sval = v.val(b);
+    if (lane == 0) {
+        *v.coords(b) = make_int4(r0, z0, r1, z1);
+        *v.offs(b) = make_int4((int)wr.a, (int)wc.a, (int)wv.a, 0);
+        const uint32_t bytes = (uint32_t)((wr.e - wr.a) * 4 + (wc.e - wc.a) * 4 + (wv.e - wv.a) * (long long)sizeof(TV));
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(v.bar(b), bytes);
+        if (wr.e > wr.a) bulk_copy_g2s(srp, a.row_ptr + wr.a, (uint32_t)((wr.e - wr.a) * 4), v.bar(b));
+        if (wc.e > wc.a) bulk_copy_g2s(scol, a.col_ind + wc.a, (uint32_t)((wc.e - wc.a) * 4), v.bar(b));
+        if (wv.e > wv.a)
+            bulk_copy_g2s(sval, static_cast<const TV*>(a.vals) + wv.a, (uint32_t)((wv.e - wv.a) * sizeof(TV)), v.bar(b));
+    }
+    // array tails not covered by the aligned bulk copies
+    {
+        const long long i = (wr.e > r0 ? wr.e : r0) + lane;
+        if (i < (long long)r1 + 1) srp[i - wr.a] = a.row_ptr[i];
+    }
+    {
+        const long long i = (wc.e > z0 ? wc.e : z0) + lane;
+        if (i < z1) scol[i - wc.a] = a.col_ind[i];
+    }
+    {
+        const long long i = (wv.e > z0 ? wv.e : z0) + lane;
+        if (i < z1) sval[i - wv.a] = static_cast<const TV*>(a.vals)[i];
+    }
+}
+
+// Cooperative (all threads) load of a tile's windows, used when an array
+// base is not 16-byte aligned.  Uses the same smem indexing as merge_stage.
+template <typename TV, int VEC, int W>
+__device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
+    const int tile = item % a.num_tiles;
+    const int2 l0 = a.limits[tile], l1 = a.limits[tile + 1];
+    const int r0 = l0.x, z0 = l0.y, r1 = l1.x, z1 = l1.y;
+    if (threadIdx.x == 0) {
+        *v.coords(b) = make_int4(r0, z0, r1, z1);
+        *v.offs(b) = make_int4(r0, z0, z0, 0);
+    }
+    int* srp = v.rp(b);
+    int* scol = v.col(b);
+    TV* sval = v.val(b);
+    for (int i = r0 + threadIdx.x; i <= r1; i += blockDim.x) srp[i - r0] = a.row_ptr[i];
+    for (int i = z0 + threadIdx.x; i < z1; i += blockDim.x) {
+        scol[i - z0] = a.col_ind[i];
+        sval[i - z0] = static_cast<const TV*>(a.vals)[i];
+    }
+}
+
+// Phase 2 of Algorithm 1 for one tile held in staging buffer b.
+//
+// Inside the tile every lane group takes an equal share of the tile's path
+// items (a second merge-path search, in shared memory) and walks it: a
+// nonzero adds val * B[col, slab] to the running sum; a row end emits the sum
+// (PREPARESPMM / REDUCETOGLOBALSPMM).  The first row a group emits may have
+// begun in an earlier group, so it is held back in shared memory together with
+// every group's trailing partial sum (its carry-out) and combined after a
+// barrier.  Of the tile as a whole, the partial sum of a row that began in an
+// earlier tile (head) and of the row left unfinished at its end (carry) go to
+// global memory for the fix-up pass.
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
+    using L = MergeSmem<TV, VEC, W>;
+    constexpr int U = kUnroll;
+    constexpr int CV = (U > W) ? U / W : 1;
+    constexpr int BS = W * CV;
+    constexpr int G = BS / U;
+    const int tile = item % a.num_tiles;
+    const int slab = item / a.num_tiles;
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (W - 1);
+    const int s = threadIdx.x / W;  // lane group
+    const long long col0 = (long long)slab * L::SW + (long long)sl * VEC;
+    const bool col_ok = col0 < a.n;
+    const int4 cz = *v.coords(b);
+    const int4 of = *v.offs(b);
+    const int r0 = cz.x, z0 = cz.y, r1 = cz.z, z1 = cz.w;
+    const int* srp = v.rp(b) - of.x;    // srp[i] = row_ptr[i] for i in [r0, r1]
+    const int* scol = v.col(b) - of.y;  // scol[p] = col_ind[p] for p in [z0, z1)
+    const TV* sval = v.val(b) - of.z;
+    const TB* __restrict__ B = static_cast<const TB*>(a.B);
+    TC* __restrict__ C = static_cast<TC*>(a.C);
+    const int rows_t = r1 - r0, nz_t = z1 - z0, items = rows_t + nz_t;
+
+    // this group's share of the tile's path
+    auto search = [&](int d) {
+        int lo = d - nz_t > 0 ? d - nz_t : 0, hi = d < rows_t ? d : rows_t;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (srp[r0 + mid + 1] <= z0 + d - mid - 1) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int ds = min(s * a.ips, items), de = min((s + 1) * a.ips, items);
+    const int xs = search(ds), xe = search(de);
+    int row = r0 + xs;
+    const int z_s = z0 + ds - xs;
+    const int row_e = r0 + xe, z_e = z0 + de - xe;
+    int rend = row < r1 ? srp[row + 1] : INT_MAX;
+    int first_row = -1;
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+
+    auto emit = [&]() {
+        if (first_row < 0) {
+            first_row = row;
+            if (col_ok) {
+                float* f = v.first(s) + sl * VEC;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) f[e] = acc[e];
+            }
+        } else if (col_ok) {
+            store_vec<TC, VEC>(C + (long long)row * a.ldc + col0, acc);
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+        ++row;
+        rend = row < r1 ? srp[row + 1] : INT_MAX;
+    };
+
+    const int nb = (z_e - z_s + BS - 1) / BS;
+    const int nb_max = __reduce_max_sync(kFullMask, nb);
+    for (int bt = 0; bt < nb_max; ++bt) {
+        const int base = z_s + bt * BS;
+        const int cnt = z_e - base;
+        int mc[CV];
+        float mv[CV];
+#pragma unroll
+        for (int c = 0; c < CV; ++c) {
+            const int p = base + c * W + sl;
+            const bool ok = p < z_e;
+            mc[c] = ok ? scol[p] : 0;
+            mv[c] = ok ? Elem<TV>::to_f(sval[p]) : 0.0f;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g > 0 && __all_sync(kFullMask, g * U >= cnt)) break;
+            Raw<TB, VEC> bv[U];
+            float vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = g * U + u;
+                const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
+                vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = g * U + u;
+                if (j < cnt) {
+                    const int p = base + j;
+                    while (p >= rend) emit();  // rows (possibly empty) that end before nonzero p
+                    fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+                }
+            }
+        }
+    }
+    while (row < row_e) emit();  // row ends after the group's last nonzero
+    if (col_ok) {
+        float* cpart = v.carry(s) + sl * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) cpart[e] = acc[e];
+    }
+    if (sl == 0) {
+        v.first_row()[s] = first_row;
+        v.carry_row()[s] = row;
+    }
+    __syncthreads();
+
+    // combine: a group's first emitted row adds the carries of the groups before it
+    const bool head_exists = r0 < r1 && srp[r0] < z0;  // row r0 began in an earlier tile and ends here
+    const int fr = v.first_row()[s];
+    if (fr >= 0 && col_ok) {
+        int t = s - 1;
+        while (t >= 0 && v.carry_row()[t] == fr) --t;
+        float sum[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sum[e] = 0.0f;
+        for (int u = t + 1; u < s; ++u) {
+            const float* c = v.carry(u) + sl * VEC;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) sum[e] += c[e];
+        }
+        const float* f = v.first(s) + sl * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sum[e] += f[e];
+        if (fr == r0 && head_exists) {
+            float* h = a.head + (size_t)tile * a.n + col0;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) h[e] = sum[e];
+        } else {
+            store_vec<TC, VEC>(C + (long long)fr * a.ldc + col0, sum);
+        }
+    }
+    // the tile's carry-out: the row left unfinished at the tile's end
+    const bool carry_exists = r1 < a.m && z1 > srp[r1];
+    if (s == L::S - 1 && carry_exists && col_ok) {
+        int t = s;
+        while (t > 0 && v.carry_row()[t - 1] == r1) --t;
+        float sum[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sum[e] = 0.0f;
+        for (int u = t; u <= s; ++u) {
+            const float* c = v.carry(u) + sl * VEC;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) sum[e] += c[e];
+        }
+        float* cg = a.carry + (size_t)tile * a.n + col0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) cg[e] = sum[e];
+    }
+    if (slab == 0 && threadIdx.x == 0) {
+        a.head_row[tile] = head_exists ? r0 : -1;
+        a.carry_row[tile] = carry_exists ? r1 : -1;
+    }
+}
+
+// Phase 2 driver: persistent CTAs walk the work items (slab-major, so the
+// CTAs running together gather from the same slab of B), with the next item's
+// windows brought into the other staging buffer by TMA while the current one
+// is computed.  Every mbarrier wait is bounded: when one runs out the kernel
+// records SPMM_ERR_TIMEOUT, waits (bounded) for its copies still in flight
+// and returns.
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    MergeView<TV, VEC, W> v{smem, a.ips};
+    const int total = a.num_tiles * a.slabs;
+    int item = blockIdx.x;
+    if (item >= total) return;
+    const int warp = threadIdx.x >> 5;
+    if (!a.use_tma) {
+        for (; item < total; item += gridDim.x) {
+            merge_load_plain<TV, VEC, W>(a, v, item, 0);
+            __syncthreads();
+            merge_tile<TV, TB, TC, VEC, W>(a, v, item, 0);
+            __syncthreads();
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(v.bar(0), 1);
+        mbar_init(v.bar(1), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0u;   // bit b: parity of the next phase of buffer b's mbarrier
+    uint32_t pending = 0u; // bit b: a copy into buffer b is in flight
+    if (warp == 0) merge_stage<TV, VEC, W>(a, v, item, 0);
+    pending |= 1u;
+    for (int it = 0; item < total; ++it, item += gridDim.x) {
+        const int b = it & 1;
+        const int nxt = item + gridDim.x;
+        if (nxt < total) {
+            if (warp == 0) merge_stage<TV, VEC, W>(a, v, nxt, b ^ 1);
+            pending |= 2u >> b;  // bit (b ^ 1)
+        }
+        const uint32_t par = (phase >> b) & 1u;
+        const bool ok = mbar_wait_bounded(v.bar(b), par, a.wait_ns);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) report(a.status, SPMM_ERR_TIMEOUT);
+            // let the copies still in flight land before shared memory is released
+            if (!ok) mbar_wait_bounded(v.bar(b), par, a.wait_ns);
+            if (pending & (2u >> b)) mbar_wait_bounded(v.bar(b ^ 1), (phase >> (b ^ 1)) & 1u, a.wait_ns);
+            return;
+        }
+        phase ^= 1u << b;
+        pending &= ~(1u << b);
+        merge_tile<TV, TB, TC, VEC, W>(a, v, item, b);
+        __syncthreads();
+    }
+}
+
+// FIXCARRYOUT of Algorithm 1.  For every run of consecutive tiles whose
+// carry-out belongs to the same row R (a row spanning several tiles), the row
+// is finished by the tile right after the run, which left R's remaining
+// partial sum in head[]; C[R] = carries (in tile order) + head, rounded once.
+// One CTA per tile; only run heads do work.
+template <typename TC>
+__global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int* __restrict__ head_row,
+                                   const float* __restrict__ carry, const float* __restrict__ head, int num_tiles,
+                                   int n, TC* __restrict__ C, long long ldc, int* status) {
+    const int i = blockIdx.x;
+    const int R = carry_row[i];
+    if (R < 0 || (i > 0 && carry_row[i - 1] == R)) return;
+    int j = i;
+    while (j + 1 < num_tiles && carry_row[j + 1] == R) ++j;
+    if (j + 1 >= num_tiles || head_row[j + 1] != R) {
+        if (threadIdx.x == 0) report(status, SPMM_ERR_BAD_CSR);
+        return;
+    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        float sum = 0.0f;
+        for (int t = i; t <= j; ++t) sum += carry[(size_t)t * n + c];
+        sum += head[(size_t)(j + 1) * n + c];
+        C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
+    }
+}
+
+}  // namespace spmm

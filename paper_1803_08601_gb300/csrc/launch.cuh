@@ -1,0 +1,155 @@
+// Host-side launchers of the SpMM kernels, one set per (vals, B, C) element
+// type combination.  Each combination is instantiated in its own translation
+// unit (inst_*.cu) so the library builds in parallel.
+#pragma once
+
+#include <atomic>
+
+#include "kernels.cuh"
+
+namespace spmm {
+
+// Launch shape chosen by the host: vec = elements per lane access (1 or the
+// 16-byte width of B's type), W = lanes per row, slabs = column slabs,
+// ips = merge-path items per lane group.
+struct Shape {
+    int vec;
+    int W;
+    int slabs;
+    int ips;
+};
+
+extern std::atomic<long long> g_launches;
+
+using RowSplitFn = cudaError_t (*)(const RowSplitArgs&, const Shape&, cudaStream_t);
+using MergeFn = cudaError_t (*)(const MergeArgs&, const Shape&, int grid_cap, cudaStream_t);
+using MergeSmemFn = size_t (*)(const Shape&);
+
+struct Launchers {
+    RowSplitFn rowsplit;
+    MergeFn merge;
+    MergeSmemFn merge_smem;
+};
+
+// defined in inst_*.cu
+Launchers launchers_f32_f32_f32();
+Launchers launchers_bf16_bf16_bf16();
+Launchers launchers_bf16_bf16_f32();
+Launchers launchers_bf16_f16_f16();
+Launchers launchers_bf16_f16_f32();
+Launchers launchers_f16_f16_f16();
+Launchers launchers_f16_f16_f32();
+
+// ---------------------------------------------------------------------------- templates
+
+template <typename TV, typename TB, typename TC, int VEC, int W>
+cudaError_t rowsplit_launch_one(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
+    const long long rows_per_cta = kThreads / W;
+    const long long gx = (a.m + rows_per_cta - 1) / rows_per_cta;
+    if (gx > 0x7fffffffLL || s.slabs > 65535) return cudaErrorInvalidConfiguration;
+    rowsplit_kernel<TV, TB, TC, VEC, W><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+template <typename TV, typename TB, typename TC, int VEC>
+cudaError_t rowsplit_launch_vec(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
+    switch (s.W) {
+        case 1: return rowsplit_launch_one<TV, TB, TC, VEC, 1>(a, s, st);
+        case 2: return rowsplit_launch_one<TV, TB, TC, VEC, 2>(a, s, st);
+        case 4: return rowsplit_launch_one<TV, TB, TC, VEC, 4>(a, s, st);
+        case 8: return rowsplit_launch_one<TV, TB, TC, VEC, 8>(a, s, st);
+        case 16: return rowsplit_launch_one<TV, TB, TC, VEC, 16>(a, s, st);
+        case 32: return rowsplit_launch_one<TV, TB, TC, VEC, 32>(a, s, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TV, typename TB, typename TC>
+cudaError_t rowsplit_launch(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
+    constexpr int V = Elem<TB>::kVec;
+    return s.vec == 1 ? rowsplit_launch_vec<TV, TB, TC, 1>(a, s, st) : rowsplit_launch_vec<TV, TB, TC, V>(a, s, st);
+}
+
+template <typename TV, typename TB, typename TC, int VEC, int W>
+cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
+    using L = MergeSmem<TV, VEC, W>;
+    auto kern = merge_kernel<TV, TB, TC, VEC, W>;
+    const size_t smem = L::total(s.ips);
+    // per-instantiation cache of the opt-in shared-memory size and occupancy
+    static thread_local int cached_dev = -1;
+    static thread_local size_t cached_smem = 0;
+    static thread_local int cached_blocks = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != cached_dev || smem != cached_smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int blocks = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        cached_dev = dev;
+        cached_smem = smem;
+        cached_blocks = blocks < 1 ? 1 : blocks;
+    }
+    const long long items = (long long)a.num_tiles * a.slabs;
+    long long grid = (long long)cached_blocks * grid_cap;
+    if (grid > items) grid = items;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+template <typename TV, typename TB, typename TC, int VEC>
+cudaError_t merge_launch_vec(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
+    switch (s.W) {
+        case 1: return merge_launch_one<TV, TB, TC, VEC, 1>(a, s, grid_cap, st);
+        case 2: return merge_launch_one<TV, TB, TC, VEC, 2>(a, s, grid_cap, st);
+        case 4: return merge_launch_one<TV, TB, TC, VEC, 4>(a, s, grid_cap, st);
+        case 8: return merge_launch_one<TV, TB, TC, VEC, 8>(a, s, grid_cap, st);
+        case 16: return merge_launch_one<TV, TB, TC, VEC, 16>(a, s, grid_cap, st);
+        case 32: return merge_launch_one<TV, TB, TC, VEC, 32>(a, s, grid_cap, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TV, typename TB, typename TC>
+cudaError_t merge_launch(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
+    constexpr int V = Elem<TB>::kVec;
+    return s.vec == 1 ? merge_launch_vec<TV, TB, TC, 1>(a, s, grid_cap, st)
+                      : merge_launch_vec<TV, TB, TC, V>(a, s, grid_cap, st);
+}
+
+template <typename TV, int VEC>
+size_t merge_smem_vec(const Shape& s) {
+    switch (s.W) {
+        case 1: return MergeSmem<TV, VEC, 1>::total(s.ips);
+        case 2: return MergeSmem<TV, VEC, 2>::total(s.ips);
+        case 4: return MergeSmem<TV, VEC, 4>::total(s.ips);
+        case 8: return MergeSmem<TV, VEC, 8>::total(s.ips);
+        case 16: return MergeSmem<TV, VEC, 16>::total(s.ips);
+        default: return MergeSmem<TV, VEC, 32>::total(s.ips);
+    }
+}
+
+template <typename TV, typename TB, typename TC>
+size_t merge_smem(const Shape& s) {
+    constexpr int V = Elem<TB>::kVec;
+    return s.vec == 1 ? merge_smem_vec<TV, 1>(s) : merge_smem_vec<TV, V>(s);
+}
+
+template <typename TV, typename TB, typename TC>
+Launchers make_launchers() {
+    return Launchers{&rowsplit_launch<TV, TB, TC>, &merge_launch<TV, TB, TC>, &merge_smem<TV, TB, TC>};
+}
+
+}  // namespace spmm
+
+#define SPMM_DEFINE_LAUNCHERS(NAME, TV, TB, TC) \
+    namespace spmm {                            \
+    Launchers NAME() { return make_launchers<TV, TB, TC>(); } \
+    }

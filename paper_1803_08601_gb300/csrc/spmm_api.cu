@@ -1,0 +1,425 @@
+// C ABI of the SpMM library (include/spmm.h): argument checks, the Section 5.4
+// heuristic, launch-shape selection, merge workspace layout, and dispatch to
+// the per-dtype launchers.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "launch.cuh"
+
+namespace spmm {
+
+std::atomic<long long> g_launches{0};
+
+// Merge-path tiles (Section 4.2): the path that merges the row end offsets
+// row_ptr[1..m] with the nonzero indices 0..nnz-1 is cut into tiles of equal
+// length (rows + nonzeros).
+//
+// Phase 1 (PARTITIONSPMM): one thread per tile boundary finds the boundary's
+// (rows, nonzeros) coordinate by binary search on its diagonal.
+__global__ void merge_partition_kernel(const int* __restrict__ row_ptr, int m, long long nnz, int items_per_tile,
+                                       int num_tiles, int2* __restrict__ limits) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > num_tiles) return;
+    const long long total = (long long)m + nnz;
+    long long d = (long long)t * items_per_tile;
+    if (d > total) d = total;
+    long long lo = d - nnz > 0 ? d - nnz : 0;
+    long long hi = d < m ? d : m;
+    while (lo < hi) {  // number of row ends among the first d merged items
+        const long long mid = (lo + hi) >> 1;
+        if ((long long)__ldg(row_ptr + mid + 1) <= d - mid - 1) lo = mid + 1;
+        else hi = mid;
+    }
+    limits[t] = make_int2((int)lo, (int)(d - lo));
+}
+
+// Bounded-wait self test: waits on a phase that nothing completes.
+__global__ void bounded_wait_probe_kernel(int* status, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) report(status, SPMM_ERR_TIMEOUT);
+}
+
+
+namespace {
+
+constexpr double kPaperThreshold = 9.35;  // Section 5.4
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per bounded wait
+constexpr size_t kMaxSmem = 200 * 1024;  // dynamic shared memory the merge kernel may request
+
+struct TypeCombo {
+    int tv, tb, tc;
+    Launchers (*make)();
+};
+
+const TypeCombo kCombos[] = {
+    {SPMM_F32, SPMM_F32, SPMM_F32, &launchers_f32_f32_f32},
+    {SPMM_BF16, SPMM_BF16, SPMM_BF16, &launchers_bf16_bf16_bf16},
+    {SPMM_BF16, SPMM_BF16, SPMM_F32, &launchers_bf16_bf16_f32},
+    {SPMM_BF16, SPMM_F16, SPMM_F16, &launchers_bf16_f16_f16},
+    {SPMM_BF16, SPMM_F16, SPMM_F32, &launchers_bf16_f16_f32},
+    {SPMM_F16, SPMM_F16, SPMM_F16, &launchers_f16_f16_f16},
+    {SPMM_F16, SPMM_F16, SPMM_F32, &launchers_f16_f16_f32},
+};
+
+const Launchers* find_launchers(int tv, int tb, int tc) {
+    static Launchers table[sizeof(kCombos) / sizeof(kCombos[0])];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (size_t i = 0; i < sizeof(kCombos) / sizeof(kCombos[0]); ++i) table[i] = kCombos[i].make();
+    });
+    for (size_t i = 0; i < sizeof(kCombos) / sizeof(kCombos[0]); ++i)
+        if (kCombos[i].tv == tv && kCombos[i].tb == tb && kCombos[i].tc == tc) return &table[i];
+    return nullptr;
+}
+
+int dtype_size(int t) { return t == SPMM_F32 ? 4 : (t == SPMM_BF16 || t == SPMM_F16) ? 2 : 0; }
+
+int pow2_ceil(long long x) {
+    int p = 1;
+    while (p < x && p < 32) p <<= 1;
+    return p;
+}
+
+double threshold_of(const spmm_tuning_t* t) {
+    return (t && t->merge_threshold > 0.0) ? t->merge_threshold : kPaperThreshold;
+}
+
+int resolve_alg(int alg, int m, long long nnz, const spmm_tuning_t* t) {
+    if (alg != SPMM_ALG_AUTO) return alg;
+    return spmm_select_alg(m, nnz, threshold_of(t));
+}
+
+// Launch shape for a given access width.  The lane group of a row covers
+// W * vec columns; W is the smallest power of two whose group spans the
+// columns of one slab.
+bool shape_for(int n, int vec, const spmm_tuning_t* t, Shape* s) {
+    s->vec = vec;
+    const long long chunks = ((long long)n + vec - 1) / vec;
+    int W;
+    if (t && t->lanes_per_row > 0) {
+        W = t->lanes_per_row;
+        if (W > 32 || (W & (W - 1))) return false;
+    } else if (t && t->column_slabs > 0) {
+        W = pow2_ceil((chunks + t->column_slabs - 1) / t->column_slabs);
+    } else {
+        W = pow2_ceil(chunks);
+    }
+    s->W = W;
+    s->slabs = (int)((chunks + W - 1) / W);
+    if (s->slabs > 65535) return false;
+    const int groups = kThreads / W;
+    int ips = (t && t->items_per_subwarp > 0) ? t->items_per_subwarp : 2048 / groups;
+    if (ips < 4) ips = 4;
+    if (ips > 4096) ips = 4096;
+    s->ips = ips;
+    return true;
+}
+
+// 16-byte accesses when n, both leading dimensions and both base pointers allow them.
+bool choose_shape(int n, int tb, int tc, const void* B, long long ldb, const void* C, long long ldc,
+                  const spmm_tuning_t* t, Shape* s) {
+    const int V = 16 / dtype_size(tb);
+    const bool vec_ok = n % V == 0 && ldb % V == 0 && ldc % V == 0 && ((uintptr_t)B % 16) == 0 &&
+                        ((uintptr_t)C % (uintptr_t)(V * dtype_size(tc))) == 0;
+    return shape_for(n, vec_ok ? V : 1, t, s);
+}
+
+struct MergeLayout {
+    int num_tiles;
+    size_t off_limits, off_carry_row, off_head_row, off_carry, off_head, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
+    MergeLayout L{};
+    const long long ipt = (long long)(kThreads / s.W) * s.ips;
+    const long long total = (long long)m + nnz;
+    L.num_tiles = (int)((total + ipt - 1) / ipt);
+    size_t off = 0;
+    L.off_limits = off;
+    off = align256(off + (size_t)(L.num_tiles + 1) * sizeof(int2));
+    L.off_carry_row = off;
+    off = align256(off + (size_t)L.num_tiles * 4);
+    L.off_head_row = off;
+    off = align256(off + (size_t)L.num_tiles * 4);
+    L.off_carry = off;
+    off = align256(off + (size_t)L.num_tiles * n * 4);
+    L.off_head = off;
+    off = align256(off + (size_t)L.num_tiles * n * 4);
+    L.total = off;
+    return L;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+// Shrink the merge tile until the double-buffered staging fits one CTA's
+// shared memory (sv = bytes per value; the float32 bound covers 16-bit vals).
+void clamp_tile(Shape* s, int sv) {
+    auto bytes = [&](const Shape& t) -> size_t {
+        if (sv == 4) return t.vec == 1 ? merge_smem_vec<float, 1>(t) : t.vec == 4 ? merge_smem_vec<float, 4>(t) : merge_smem_vec<float, 8>(t);
+        return t.vec == 1 ? merge_smem_vec<__half, 1>(t) : t.vec == 4 ? merge_smem_vec<__half, 4>(t) : merge_smem_vec<__half, 8>(t);
+    };
+    while (s->ips > 4 && bytes(*s) > kMaxSmem) s->ips = s->ips * 3 / 4;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SPMM_OK;
+    if (e == cudaErrorMemoryAllocation) return SPMM_ERR_ALLOC;
+    if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources || e == cudaErrorInvalidValue)
+        return SPMM_ERR_LAUNCH;
+    return SPMM_ERR_CUDA;
+}
+
+// Checks of everything a host can see.  Returns SPMM_OK or an error status.
+int check_args(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
+               const void* B, long long ldb, const void* C, long long ldc, int alg) {
+    if (m < 0 || k < 0 || n < 0 || nnz < -1 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
+    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_MERGE) return SPMM_ERR_INVALID_VALUE;
+    if (m > 0 && n > 0) {
+        if (!row_ptr || !C) return SPMM_ERR_INVALID_VALUE;
+        if (ldc < n) return SPMM_ERR_INVALID_VALUE;
+        if (nnz != 0 && (!col_ind || !vals)) return SPMM_ERR_INVALID_VALUE;
+        if (nnz != 0 && k > 0 && (!B || ldb < n)) return SPMM_ERR_INVALID_VALUE;
+        if (nnz > 0 && k == 0) return SPMM_ERR_INVALID_VALUE;  // a nonzero needs a column
+    }
+    return SPMM_OK;
+}
+
+int read_nnz(const int* row_ptr, int m, cudaStream_t st, long long* nnz) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, row_ptr + m, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (v < 0) return SPMM_ERR_BAD_CSR;
+    *nnz = v;
+    return SPMM_OK;
+}
+
+}  // namespace
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" {
+
+const char* spmm_status_string(int status) {
+    switch (status) {
+        case SPMM_OK: return "SPMM_OK";
+        case SPMM_ERR_INVALID_VALUE: return "SPMM_ERR_INVALID_VALUE: invalid size, pointer, stride or enum";
+        case SPMM_ERR_ALLOC: return "SPMM_ERR_ALLOC: device memory allocation failed";
+        case SPMM_ERR_LAUNCH: return "SPMM_ERR_LAUNCH: kernel launch rejected";
+        case SPMM_ERR_BAD_CSR: return "SPMM_ERR_BAD_CSR: inconsistent CSR structure";
+        case SPMM_ERR_TIMEOUT: return "SPMM_ERR_TIMEOUT: a bounded device-side wait ran out";
+        case SPMM_ERR_UNSUPPORTED: return "SPMM_ERR_UNSUPPORTED: dtype combination not provided";
+        case SPMM_ERR_CUDA: return "SPMM_ERR_CUDA: CUDA runtime error";
+        case SPMM_ERR_WORKSPACE: return "SPMM_ERR_WORKSPACE: workspace missing or too small";
+        default: return "unknown status";
+    }
+}
+
+int spmm_version(void) { return 100; }
+
+long long spmm_launch_count(void) { return g_launches.load(); }
+
+int spmm_select_alg(int m, long long nnz, double threshold) {
+    if (m <= 0) return SPMM_ALG_ROW_SPLIT;
+    if (threshold <= 0.0) threshold = kPaperThreshold;
+    const double d = (double)nnz / (double)m;  // mean row length (Section 5.4)
+    return d < threshold ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT;
+}
+
+size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int b_type, const spmm_tuning_t* tuning) {
+    if (m < 0 || k < 0 || n < 0 || nnz < 0 || dtype_size(b_type) == 0) return 0;
+    if (resolve_alg(alg, m, nnz, tuning) != SPMM_ALG_MERGE || m == 0 || n == 0) return 0;
+    // the access width depends on pointer alignment, unknown here: size for both widths
+    size_t best = 0;
+    for (int vec : {1, 16 / dtype_size(b_type)}) {
+        Shape s;
+        if (!shape_for(n, vec, tuning, &s)) return 0;
+        clamp_tile(&s, 4);
+        const size_t need = merge_layout(m, nnz, n, s).total;
+        if (need > best) best = need;
+    }
+    return best;
+}
+
+int spmm_merge_partition(int m, long long nnz, const int* row_ptr, int items_per_tile, int num_tiles, int* limits,
+                         void* stream) {
+    if (m < 0 || nnz < 0 || items_per_tile <= 0 || num_tiles < 0 || !limits || (m > 0 && !row_ptr))
+        return SPMM_ERR_INVALID_VALUE;
+    if ((long long)num_tiles * items_per_tile < (long long)m + nnz) return SPMM_ERR_INVALID_VALUE;
+    const int threads = 256;
+    const int blocks = (num_tiles + 1 + threads - 1) / threads;
+    merge_partition_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(row_ptr, m, nnz, items_per_tile, num_tiles,
+                                                                         reinterpret_cast<int2*>(limits));
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cuda_status(e);
+}
+
+int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
+                int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
+                const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes, int* d_status, void* stream) {
+    int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
+    if (st != SPMM_OK) return st;
+    const Launchers* L = find_launchers(vals_type, b_type, c_type);
+    if (!L) return SPMM_ERR_UNSUPPORTED;
+    if (m == 0 || n == 0) return SPMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nnz < 0) {
+        st = read_nnz(row_ptr, m, s, &nnz);
+        if (st != SPMM_OK) return st;
+    }
+    Shape shape;
+    if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, tuning, &shape)) return SPMM_ERR_INVALID_VALUE;
+    const int a = resolve_alg(alg, m, nnz, tuning);
+    if (a == SPMM_ALG_ROW_SPLIT) {
+        RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
+        return cuda_status(L->rowsplit(ra, shape, s));
+    }
+
+    // merge based: partition, compute, fix-up.  Tiles are capped so that the
+    // double-buffered staging fits the shared memory of one CTA.
+    clamp_tile(&shape, dtype_size(vals_type));
+    if (L->merge_smem(shape) > kMaxSmem) return SPMM_ERR_INVALID_VALUE;
+    const MergeLayout lay = merge_layout(m, nnz, n, shape);
+    bool own = false;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    if (!ws) {
+        if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocAsync(&p, lay.total, s);
+        if (e != cudaSuccess) return SPMM_ERR_ALLOC;
+        ws = static_cast<unsigned char*>(p);
+        own = true;
+    } else if (workspace_bytes < lay.total || ((uintptr_t)ws % 256) != 0) {
+        return SPMM_ERR_WORKSPACE;
+    }
+    MergeArgs ma{};
+    ma.m = m;
+    ma.n = n;
+    ma.nnz = nnz;
+    ma.row_ptr = row_ptr;
+    ma.col_ind = col_ind;
+    ma.vals = vals;
+    ma.B = B;
+    ma.ldb = ldb;
+    ma.C = C;
+    ma.ldc = ldc;
+    ma.limits = reinterpret_cast<const int2*>(ws + lay.off_limits);
+    ma.num_tiles = lay.num_tiles;
+    ma.slabs = shape.slabs;
+    ma.ips = shape.ips;
+    ma.carry = reinterpret_cast<float*>(ws + lay.off_carry);
+    ma.head = reinterpret_cast<float*>(ws + lay.off_head);
+    ma.carry_row = reinterpret_cast<int*>(ws + lay.off_carry_row);
+    ma.head_row = reinterpret_cast<int*>(ws + lay.off_head_row);
+    ma.status = d_status;
+    ma.use_tma = ((uintptr_t)row_ptr % 16 == 0) && ((uintptr_t)col_ind % 16 == 0) && ((uintptr_t)vals % 16 == 0);
+    ma.wait_ns = kWaitLimitNs;
+
+    const int ipt = (kThreads / shape.W) * shape.ips;
+    st = spmm_merge_partition(m, nnz, row_ptr, ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
+                              stream);
+    if (st == SPMM_OK) st = cuda_status(L->merge(ma, shape, sm_count(), s));
+    if (st == SPMM_OK && lay.num_tiles > 1) {
+        auto fix = [&](auto* c) {
+            using TC = std::remove_pointer_t<decltype(c)>;
+            merge_fixup_kernel<TC><<<lay.num_tiles, 128, 0, s>>>(ma.carry_row, ma.head_row, ma.carry, ma.head,
+                                                                 lay.num_tiles, n, static_cast<TC*>(C), ldc, d_status);
+        };
+        if (c_type == SPMM_F32) fix(static_cast<float*>(nullptr));
+        else if (c_type == SPMM_BF16) fix(static_cast<__nv_bfloat16*>(nullptr));
+        else fix(static_cast<__half*>(nullptr));
+        const cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+        st = cuda_status(e);
+    }
+    if (own) {
+        const cudaError_t e = cudaFreeAsync(ws, s);
+        if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    }
+    return st;
+}
+
+int spmm_csr(int m, int k, int n, const int* row_ptr, const int* col_ind, const float* vals, const float* B,
+             long long ldb, float* C, long long ldc, int alg, void* stream) {
+    return spmm_csr_ex(m, k, n, -1, row_ptr, col_ind, vals, SPMM_F32, B, SPMM_F32, ldb, C, SPMM_F32, ldc, alg,
+                       nullptr, nullptr, 0, nullptr, stream);
+}
+
+int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                  const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
+                  const spmm_tuning_t* tuning, void* stream) {
+    if (m < 0 || k < 0 || n < 0) return SPMM_ERR_INVALID_VALUE;
+    if (m > 0 && !row_ptr) return SPMM_ERR_INVALID_VALUE;
+    const long long nnz = m > 0 ? row_ptr[m] : 0;
+    int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
+    if (st != SPMM_OK) return st;
+    const int sv = dtype_size(vals_type), sb = dtype_size(b_type), sc = dtype_size(c_type);
+    if (!find_launchers(vals_type, b_type, c_type)) return SPMM_ERR_UNSUPPORTED;
+    if (m == 0 || n == 0) return SPMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // device copies: B and C packed with leading dimension n (rounded to 16 bytes for the vector path)
+    const long long vb = 16 / sb, vc = 16 / sc;
+    const long long ldb_d = (n + vb - 1) / vb * vb, ldc_d = (n + vc - 1) / vc * vc;
+    const size_t b_rp = align256((size_t)(m + 1) * 4), b_col = align256((size_t)nnz * 4),
+                 b_val = align256((size_t)nnz * sv), b_B = align256((size_t)k * ldb_d * sb),
+                 b_C = align256((size_t)m * ldc_d * sc);
+    void* mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, b_rp + b_col + b_val + b_B + b_C, s);
+    if (e != cudaSuccess) return SPMM_ERR_ALLOC;
+    unsigned char* base = static_cast<unsigned char*>(mem);
+    int* d_rp = reinterpret_cast<int*>(base);
+    int* d_col = reinterpret_cast<int*>(base + b_rp);
+    void* d_val = base + b_rp + b_col;
+    void* d_B = base + b_rp + b_col + b_val;
+    void* d_C = base + b_rp + b_col + b_val + b_B;
+    e = cudaMemcpyAsync(d_rp, row_ptr, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col_ind, (size_t)nnz * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, vals, (size_t)nnz * sv, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && k > 0 && nnz > 0)
+        e = cudaMemcpy2DAsync(d_B, (size_t)ldb_d * sb, B, (size_t)ldb * sb, (size_t)n * sb, (size_t)k,
+                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        st = spmm_csr_ex(m, k, n, nnz, d_rp, d_col, d_val, vals_type, d_B, b_type, ldb_d, d_C, c_type, ldc_d, alg,
+                         tuning, nullptr, 0, nullptr, stream);
+    else
+        st = cuda_status(e);
+    if (st == SPMM_OK) {
+        e = cudaMemcpy2DAsync(C, (size_t)ldc * sc, d_C, (size_t)ldc_d * sc, (size_t)n * sc, (size_t)m,
+                              cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    e = cudaFreeAsync(mem, s);
+    if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    e = cudaStreamSynchronize(s);
+    if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    return st;
+}
+
+int spmm_debug_bounded_wait(int* d_status, long long limit_ns, void* stream) {
+    if (!d_status) return SPMM_ERR_INVALID_VALUE;
+    if (limit_ns < 1000) limit_ns = 1000;
+    if (limit_ns > 2000000000LL) limit_ns = 2000000000LL;
+    bounded_wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(d_status, (unsigned long long)limit_ns);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cuda_status(e);
+}
+
+}  // extern "C"

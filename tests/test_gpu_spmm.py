@@ -1,0 +1,209 @@
+"""GPU parity of the FP32 SpMM paths (row split, merge based, heuristic) with
+the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from spmm_cases import FP32_TOL, STRUCTURES, check, csr_arrays, structure
+
+pytestmark = pytest.mark.gpu
+
+ALGS = ["row_split", "merge", "auto"]
+
+
+def to_dev(torch, *arrays):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+
+
+def run(pkg, torch, rp, ci, v, B, alg, **kw):
+    d_rp, d_ci, d_v = to_dev(torch, rp, ci, v)
+    d_B = B if isinstance(B, torch.Tensor) else to_dev(torch, B)[0]
+    C = pkg.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=int(rp[-1]), **kw)
+    torch.cuda.synchronize()
+    return C
+
+
+@pytest.mark.parametrize("name", STRUCTURES)
+@pytest.mark.parametrize("alg", ALGS)
+@pytest.mark.parametrize("n", [1, 8, 13, 64, 128, 300])
+def test_structures(gpu_lib, name, alg, n):
+    import torch
+
+    rp, ci, v, k = structure(name)
+    B = gen.normal_matrix(k, n, 11 + n)
+    C = run(gpu_lib, torch, rp, ci, v, B, alg)
+    assert C.shape == (len(rp) - 1, n)
+    check(C.cpu().numpy(), rp, ci, v, B)
+
+
+@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("n", [4, 32, 64, 96, 256])
+def test_exact_integer_arithmetic_is_bitwise(gpu_lib, alg, n):
+    """Integer vals in [-2, 2] and B in [-4, 4] with rows of up to 10^4 terms: every
+    partial sum is an integer below 2^24, so float32 must equal the oracle exactly,
+    whatever the summation order (this pins the carry-out / fix-up arithmetic)."""
+    import torch
+
+    rng = np.random.default_rng(n)
+    lens = rng.integers(0, 300, 3000)
+    lens[::97] = 10_000
+    rp, ci, v = csr_arrays(lens, 12_000, 5, int_vals=True)
+    B = rng.integers(-4, 5, size=(12_000, n)).astype(np.float32)
+    for ips in (4, 37, 0):
+        C = run(gpu_lib, torch, rp, ci, v, B, alg, tuning=dict(items_per_subwarp=ips))
+        assert np.array_equal(C.cpu().numpy(), oracle.spmm(rp, ci, v, B).astype(np.float32))
+
+
+def test_identity_and_permutation_are_exact(gpu_lib):
+    import torch
+
+    for name in ("identity", "permutation"):
+        rp, ci, v, k = structure(name)
+        B = gen.normal_matrix(k, 64, 3)
+        for alg in ALGS:
+            C = run(gpu_lib, torch, rp, ci, v, B, alg).cpu().numpy()
+            assert np.array_equal(C, B[ci])
+
+
+@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("tuning", [dict(lanes_per_row=4), dict(lanes_per_row=32), dict(column_slabs=4),
+                                    dict(column_slabs=2, items_per_subwarp=9), dict(items_per_subwarp=4),
+                                    dict(items_per_subwarp=700), dict(lanes_per_row=1, items_per_subwarp=5)])
+def test_launch_shapes(gpu_lib, alg, tuning):
+    import torch
+
+    rp, ci, v, k = structure("power_law", seed=2)
+    B = gen.normal_matrix(k, 64, 5)
+    C = run(gpu_lib, torch, rp, ci, v, B, alg, tuning=tuning)
+    check(C.cpu().numpy(), rp, ci, v, B)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_strides_and_scalar_path(gpu_lib, alg):
+    """ldb > n, ldc > n, and a B whose base is not 16-byte aligned (scalar path)."""
+    import torch
+
+    rp, ci, v, k = structure("short_rows")
+    n = 48
+    Bbig = gen.normal_matrix(k, 70, 8)
+    d_big = torch.from_numpy(Bbig).cuda()
+    out = torch.full((len(rp) - 1, 61), 7.0, device="cuda")
+    for Bview, ref_B in ((d_big[:, :n], Bbig[:, :n]), (d_big[:, 1:n + 1], Bbig[:, 1:n + 1])):
+        C = run(gpu_lib, torch, rp, ci, v, Bview, alg, out=out[:, 3:3 + n])
+        check(C.cpu().numpy(), rp, ci, v, np.ascontiguousarray(ref_B))
+        assert torch.all(out[:, :3] == 7.0) and torch.all(out[:, 3 + n:] == 7.0)  # padding untouched
+
+
+def test_merge_partition_matches_oracle(gpu_lib):
+    import torch
+
+    for name in ("power_law", "empty_runs", "giant_row", "all_empty", "single_row"):
+        rp, ci, v, k = structure(name)
+        d_rp = torch.from_numpy(rp).cuda()
+        for items in (1, 7, 64, 2048):
+            if (len(rp) - 1 + int(rp[-1])) // items > 2_000_000:
+                continue
+            lim = gpu_lib.merge_partition(d_rp, items, nnz=int(rp[-1])).cpu().numpy()
+            assert np.array_equal(lim, oracle.merge_path_limits(rp, items)), (name, items)
+
+
+def test_merge_is_deterministic(gpu_lib):
+    import torch
+
+    rp, ci, v, k = structure("giant_row")
+    B = gen.normal_matrix(k, 64, 9)
+    c1 = run(gpu_lib, torch, rp, ci, v, B, "merge").cpu().numpy()
+    c2 = run(gpu_lib, torch, rp, ci, v, B, "merge").cpu().numpy()
+    assert np.array_equal(c1, c2)
+
+
+def test_explicit_workspace_and_status(gpu_lib):
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("short_rows")
+    B = gen.normal_matrix(k, 32, 2)
+    m, nnz = len(rp) - 1, int(rp[-1])
+    size = pkg.workspace_size(m, k, 32, nnz, "merge")
+    ws = torch.empty(size, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = run(pkg, torch, rp, ci, v, B, "merge", workspace=ws, status=status)
+    check(C.cpu().numpy(), rp, ci, v, B)
+    assert int(status.item()) == 0
+    with pytest.raises(pkg.SpMMError) as e:
+        run(pkg, torch, rp, ci, v, B, "merge", workspace=ws[: size // 4])
+    assert e.value.status == pkg.ERR_WORKSPACE
+
+
+def test_launch_counts(gpu_lib):
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("short_rows")
+    B = gen.normal_matrix(k, 32, 2)
+    c0 = pkg.spmm_launch_count()
+    run(pkg, torch, rp, ci, v, B, "row_split")
+    c1 = pkg.spmm_launch_count()
+    run(pkg, torch, rp, ci, v, B, "merge")
+    c2 = pkg.spmm_launch_count()
+    assert c1 - c0 == 1  # one row-split launch
+    assert c2 - c1 == 3  # partition, compute, fix-up
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(gpu_lib):
+    """A wait on an mbarrier phase that nothing completes runs out after its limit,
+    stores SPMM_ERR_TIMEOUT, and the context keeps working."""
+    import torch
+
+    pkg = gpu_lib
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert pkg.spmm_debug_bounded_wait(status.data_ptr(), 2_000_000, torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == pkg.ERR_TIMEOUT
+    rp, ci, v, k = structure("uniform16")
+    B = gen.normal_matrix(k, 16, 1)
+    check(run(pkg, torch, rp, ci, v, B, "merge").cpu().numpy(), rp, ci, v, B)
+
+
+def test_host_buffers_entry_point(gpu_lib):
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("power_law")
+    B = gen.normal_matrix(k, 64, 4)
+    for alg in ALGS:
+        C = torch.empty((len(rp) - 1, 64), dtype=torch.float32).pin_memory()
+        pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), torch.from_numpy(B), C, alg=alg)
+        check(C.numpy(), rp, ci, v, B)
+
+
+def test_plain_fp32_workload_full(gpu_lib):
+    """4096 x 4096, 16 nonzeros per row, n = 64: every element against the oracle."""
+    import torch
+
+    a, B = gen.workload_plain()
+    for alg in ALGS:
+        C = run(gpu_lib, torch, a.row_ptr, a.col_ind, a.vals, B, alg)
+        check(C.cpu().numpy(), a.row_ptr, a.col_ind, a.vals, B)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [8, 32, 64, 128])
+def test_power_law_workload_full_size_sampled(gpu_lib, n):
+    """1M x 1M power-law rows at full size, both algorithms and the heuristic;
+    checked on a seeded sample of rows that includes the longest ones."""
+    import torch
+
+    a = gen.workload_power_law()
+    B = gen.normal_matrix(a.k, n, gen.SEED_BASE + 2)
+    lens = a.row_lengths()
+    rng = np.random.default_rng(n)
+    rows = np.unique(np.concatenate([rng.choice(a.m, 3000, replace=False), np.argsort(lens)[-20:],
+                                     np.nonzero(lens == 0)[0][:50], [0, a.m - 1]]))
+    d_rp, d_ci, d_v = to_dev(torch, a.row_ptr, a.col_ind, a.vals)
+    d_B = torch.from_numpy(B).cuda()
+    for alg in ALGS:
+        C = gpu_lib.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=a.nnz)
+        torch.cuda.synchronize()
+        check(C[torch.from_numpy(rows).cuda()].cpu().numpy(), a.row_ptr, a.col_ind, a.vals, B, rows=rows)

@@ -1,0 +1,109 @@
+"""The C ABI library loads and exports every declared symbol, and its host-side
+logic (heuristic, argument checks, workspace sizing) behaves as documented.
+No call here touches a GPU: each returns before any CUDA runtime call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1803_08601_gb300 as pkg
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return pkg.load()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = declared_functions()
+    assert "spmm_csr" in decl and "spmm_csr_ex" in decl
+    raw = ctypes.CDLL(pkg.LIB_PATH)
+    for name in decl:
+        assert hasattr(raw, name), f"{name} declared in include/ but not exported"
+    assert set(pkg.exported_symbols()) <= set(decl)
+
+
+def test_status_strings_and_version(lib):
+    assert pkg.spmm_status_string(0) == "SPMM_OK"
+    for s in range(1, 9):
+        assert pkg.spmm_status_string(s).startswith("SPMM_ERR_")
+    assert pkg.spmm_version() >= 100
+
+
+@pytest.mark.parametrize("m,nnz", [(100, 934), (100, 936), (20, 187), (1, 0), (0, 0), (1000, 16000),
+                                   (1_000_000, 15_821_532), (7, 65)])
+def test_heuristic_matches_oracle(lib, m, nnz):
+    """Section 5.4: the library's choice equals the oracle's on both sides of 9.35."""
+    assert pkg.spmm_select_alg(m, nnz, 0.0) == oracle.select_alg(m, nnz)
+    assert pkg.spmm_select_alg(m, nnz, pkg.PAPER_THRESHOLD) == oracle.select_alg(m, nnz)
+
+
+def test_heuristic_custom_threshold(lib):
+    assert pkg.spmm_select_alg(100, 1500, 20.0) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg(100, 1500, 10.0) == pkg.ALG_ROW_SPLIT
+
+
+def test_argument_checks_return_before_any_device_work(lib):
+    F = pkg.F32
+    good = dict(m=4, k=4, n=4, nnz=4, row_ptr=8, col_ind=16, vals=32, vals_type=F, B=64, b_type=F, ldb=4, C=128,
+                c_type=F, ldc=4, alg=0, tuning=None, workspace=None, workspace_bytes=0, d_status=None, stream=None)
+
+    def call(**kw):
+        a = dict(good)
+        a.update(kw)
+        return pkg.spmm_csr_ex(*a.values())
+
+    assert call(m=-1) == pkg.ERR_INVALID_VALUE
+    assert call(n=-3) == pkg.ERR_INVALID_VALUE
+    assert call(ldb=3) == pkg.ERR_INVALID_VALUE
+    assert call(ldc=2) == pkg.ERR_INVALID_VALUE
+    assert call(alg=7) == pkg.ERR_INVALID_VALUE
+    assert call(row_ptr=None) == pkg.ERR_INVALID_VALUE
+    assert call(C=None) == pkg.ERR_INVALID_VALUE
+    assert call(col_ind=None) == pkg.ERR_INVALID_VALUE
+    assert call(k=0) == pkg.ERR_INVALID_VALUE  # nonzeros need columns
+    assert call(nnz=-5) == pkg.ERR_INVALID_VALUE
+    assert call(vals_type=pkg.F32, b_type=pkg.BF16) == pkg.ERR_UNSUPPORTED
+    assert call(vals_type=9) == pkg.ERR_UNSUPPORTED
+    # empty problems are accepted without touching the device
+    assert call(m=0) == pkg.OK
+    assert call(n=0) == pkg.OK
+    assert pkg.spmm_merge_partition(10, 5, 8, 0, 3, 16, None) == pkg.ERR_INVALID_VALUE
+    assert pkg.spmm_merge_partition(10, 5, 8, 4, 3, 16, None) == pkg.ERR_INVALID_VALUE  # 3 tiles x 4 < 15 items
+    assert pkg.spmm_debug_bounded_wait(None, 1000, None) == pkg.ERR_INVALID_VALUE
+
+
+def test_workspace_size(lib):
+    F = pkg.F32
+    assert pkg.spmm_csr_workspace_size(1000, 1000, 64, 16000, pkg.ALG_ROW_SPLIT, F) == 0
+    assert pkg.spmm_csr_workspace_size(1000, 1000, 64, 16000, pkg.ALG_AUTO, F) == 0  # d = 16: row split
+    w = pkg.spmm_csr_workspace_size(1000, 1000, 64, 5000, pkg.ALG_AUTO, F)  # d = 5: merge
+    assert w > 0 and w % 256 == 0
+    # carries grow with n; the tile count shrinks with more items per lane group
+    assert pkg.spmm_csr_workspace_size(10**6, 10**6, 128, 10**7, pkg.ALG_MERGE, F) > \
+        pkg.spmm_csr_workspace_size(10**6, 10**6, 8, 10**7, pkg.ALG_MERGE, F)
+    small = pkg.spmm_csr_workspace_size(10**6, 10**6, 64, 10**7, pkg.ALG_MERGE, F, dict(items_per_subwarp=512))
+    big = pkg.spmm_csr_workspace_size(10**6, 10**6, 64, 10**7, pkg.ALG_MERGE, F, dict(items_per_subwarp=16))
+    assert big > small
+    assert pkg.spmm_csr_workspace_size(-1, 1, 1, 1, pkg.ALG_MERGE, F) == 0
+
+
+def test_no_cpu_path():
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(3, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        pkg.spmm(t, t[:0], torch.zeros(0), torch.zeros(2, 2))
