@@ -164,6 +164,37 @@ int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, c
  */
 int spmm_debug_bounded_wait(int *d_status, long long limit_ns, void *stream);
 
+/*
+ * Allocation-free form of spmm_csr_ex.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at call
+ * time (plugins of a host that owns all device memory, real-time loops that
+ * must not meet allocator latency or an out-of-memory failure mid-run) and
+ * have no buffer to lend as a workspace.  Arguments are those of spmm_csr_ex
+ * without the workspace; the caller still provides every input and output.
+ *
+ * The merge-based path keeps its scratch in one fixed array of
+ * spmm_csr_static_scratch_bytes() bytes (16 MiB) in device global memory,
+ * reserved on every device that loads the library and held until the process
+ * exits.  Problems whose merge scratch (spmm_csr_workspace_size) exceeds it
+ * are rejected with SPMM_ERR_WORKSPACE before any device work.  Row split
+ * needs no scratch.  The call makes no cudaMalloc / cudaFree or other
+ * allocating call.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; nothing in
+ * it needs to start at zero, but calls that overlap on the GPU (on different
+ * streams, or from several threads) race on it: serialise them.
+ * nnz = -1 reads row_ptr[m] back (a 4-byte copy that synchronises `stream`).
+ */
+int spmm_csr_noalloc(int m, int k, int n, long long nnz, const int *row_ptr, const int *col_ind,
+                     const void *vals, int vals_type, const void *B, int b_type, long long ldb, void *C,
+                     int c_type, long long ldc, int alg, const spmm_tuning_t *tuning, int *d_status,
+                     void *stream);
+
+/* Size in bytes of the fixed scratch array used by spmm_csr_noalloc. */
+size_t spmm_csr_static_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "spmm_merge_partition": ([_i, _ll, _vp, _i, _i, _vp, _vp], _i),
     "spmm_csr_host": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
     "spmm_debug_bounded_wait": ([_vp, _ll, _vp], _i),
+    "spmm_csr_noalloc": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _vp], _i),
+    "spmm_csr_static_scratch_bytes": ([], _sz),
 }
 
 
@@ -137,6 +139,20 @@ def spmm_csr_host(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C,
 
 def spmm_debug_bounded_wait(d_status, limit_ns, stream) -> int:
     return load().spmm_debug_bounded_wait(d_status, limit_ns, stream)
+
+
+def spmm_csr_noalloc(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                     d_status, stream) -> int:
+    """spmm_csr_ex without a workspace argument, for callers that cannot allocate
+    device memory at call time: the merge scratch is a fixed device array of
+    spmm_csr_static_scratch_bytes() bytes; larger problems return ERR_WORKSPACE.
+    Calls that overlap on the GPU share that array and must be serialised."""
+    return load().spmm_csr_noalloc(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc,
+                                   alg, _tuning_ptr(tuning), d_status, stream)
+
+
+def spmm_csr_static_scratch_bytes() -> int:
+    return load().spmm_csr_static_scratch_bytes()
 
 
 def _tuning_ptr(t):
