@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="power_law", choices=["power_law", "plain"])
     p.add_argument("--n", type=int, nargs="*", default=None, help="dense widths (default 8 32 64 128)")
-    p.add_argument("--alg", default="auto", choices=["auto", "row_split", "merge"])
+    p.add_argument("--alg", default="auto_gb300", choices=["auto_gb300", "auto", "row_split", "merge"])
     p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--tuning", default=None, help='JSON spmm_tuning_t fields, e.g. {"column_slabs": 2}')
@@ -236,14 +236,18 @@ def main():
     d_v = torch.from_numpy(a.vals).to(dev)
     d_B = {n: torch.from_numpy(Bs[n]).to(dev) for n in ns}
     d_C = {n: torch.empty((m, n), dtype=torch.float32, device=dev) for n in ns}
-    alg_of = {n: (pkg.spmm_select_alg(m, nnz, 0.0) if args.alg == "auto" else pkg.alg_code(args.alg)) for n in ns}
+    max_row = pkg.max_row_length(d_rp)  # measured once; passed to the GB300 selector as a hint
+    paper_pick = {n: pkg.spmm_select_alg(m, nnz, 0.0) for n in ns}
+    gb300_pick = {n: pkg.spmm_select_alg_gb300(m, nnz, max_row, n, pkg.F32) for n in ns}
+    alg_of = {n: {"auto": paper_pick[n], "auto_gb300": gb300_pick[n]}.get(args.alg, pkg.alg_code(args.alg)) for n in ns}
     tuning_ws = json.loads(args.tuning) if args.tuning else None
     ws_bytes = max(pkg.workspace_size(m, k, n, nnz, pkg.ALG_MERGE, tuning=tuning_ws) for n in ns)
     ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.float32, device=dev)
 
-    tuning = json.loads(args.tuning) if args.tuning else None
+    tuning = dict(json.loads(args.tuning)) if args.tuning else {}
+    tuning.setdefault("max_row_len", max_row)
 
     def one(n, alg):
         pkg.spmm(d_rp, d_ci, d_v, d_B[n], alg=alg, out=d_C[n], nnz=nnz, workspace=ws, tuning=tuning)
@@ -308,16 +312,20 @@ def main():
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (gen/, seed 1805): power-law CSR, N(0,1) B",
-            "config": {"workload": label, "m": m, "k": k, "nnz": nnz, "n": ns, "alg": args.alg, "tuning": tuning,
+            "config": {"workload": label, "m": m, "k": k, "nnz": nnz, "max_row": max_row, "n": ns, "alg": args.alg,
+                       "tuning": tuning,
                        "replicas": world, "l2_flush": "2x L2 write before every step", "parallelism": "replicas"},
             "roofline": roofline, "gpu_launches": int(launches)}
     cs = clk.summary()
     if cs:
         line["clocks"] = cs
 
+    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    line["selector"] = {"paper_section_5_4": {str(n): name[paper_pick[n]] for n in ns},
+                        "gb300": {str(n): name[gb300_pick[n]] for n in ns}}
     if rank == 0 and not args.no_extras:
         line["breakdown"] = breakdown(pkg, torch, one, ns, nnz, comp, args.steps, flush, stream)
-        line["e2e"] = e2e(pkg, torch, a, ns, Bs, args)
+        line["e2e"] = e2e(pkg, torch, a, ns, Bs, args, tuning)
         if world == 1:
             g, t, nrows, thr, passes = time_oracle_sample(a, ns, Bs)
             line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
@@ -353,7 +361,7 @@ def breakdown(pkg, torch, one, ns, nnz, comp, steps, flush, stream):
     return out
 
 
-def e2e(pkg, torch, a, ns, Bs, args):
+def e2e(pkg, torch, a, ns, Bs, args, tuning):
     """The step through spmm_csr_host: pinned host A, B in; host C out; copies timed."""
     rp = torch.from_numpy(a.row_ptr).pin_memory()
     ci = torch.from_numpy(a.col_ind).pin_memory()
@@ -363,13 +371,13 @@ def e2e(pkg, torch, a, ns, Bs, args):
     h2d = sum((a.m + 1) * 4 + a.nnz * 8 + a.k * n * 4 for n in ns)
     d2h = sum(a.m * n * 4 for n in ns)
     for n in ns:
-        pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg)
+        pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning)
     torch.cuda.synchronize()
     reps = max(2, min(args.steps, 5))
     t0 = time.perf_counter()
     for _ in range(reps):
         for n in ns:
-            pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg)
+            pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning)
     t = (time.perf_counter() - t0) / reps
     flops = sum(2.0 * a.nnz * n for n in ns)
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

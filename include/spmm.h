@@ -45,7 +45,10 @@ extern "C" {
 typedef enum {
     SPMM_ALG_AUTO = 0,      /* Section 5.4 heuristic on the mean row length     */
     SPMM_ALG_ROW_SPLIT = 1, /* Section 4.1, Algorithm I                         */
-    SPMM_ALG_MERGE = 2      /* Section 4.2, Algorithm II (Algorithm 1)          */
+    SPMM_ALG_MERGE = 2,     /* Section 4.2, Algorithm II (Algorithm 1)          */
+    SPMM_ALG_AUTO_GB300 = 3 /* mean row length recalibrated on GB300 plus a
+                               longest-row guard against Type 1 imbalance
+                               (Section 3.2); see spmm_select_alg_gb300      */
 } spmm_alg_t;
 
 typedef enum {
@@ -74,7 +77,11 @@ typedef struct {
                                 a slab of B resident in L2                              */
     int items_per_subwarp;   /* merge based: merge-path items (rows + nonzeros) per
                                 lane group; a tile holds 256 / lanes_per_row groups     */
+    int reserved;            /* set to 0                                               */
     double merge_threshold;  /* heuristic threshold on nnz / m; <= 0 selects 9.35       */
+    long long max_row_len;   /* SPMM_ALG_AUTO_GB300: longest row of A when the caller
+                                knows it; 0 makes the call measure it on the device
+                                (a reduction and a 4-byte copy that synchronises)       */
 } spmm_tuning_t;
 
 /* Human-readable name of a status code (static storage). */
@@ -94,6 +101,26 @@ long long spmm_launch_count(void);
  * Pure host function.
  */
 int spmm_select_alg(int m, long long nnz, double threshold);
+
+/*
+ * GB300 selector (SPMM_ALG_AUTO_GB300), pure host function.  Returns
+ * SPMM_ALG_MERGE when either
+ *   - the longest row is long enough to be the critical path of row split
+ *     (Type 1 imbalance, Section 3.2): max_row_len > 1024 and
+ *     max_row_len * 4096 > nnz, or
+ *   - the mean row length nnz / m is below 5 and a row of B is at least 64
+ *     bytes (n * element size of B); measured crossover of the two kernels on
+ *     GB300 for uniform rows (the paper's 9.35 was measured on a K40c);
+ * and SPMM_ALG_ROW_SPLIT otherwise.  m == 0 returns row split.
+ */
+int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type);
+
+/*
+ * Longest row of A (max over i of row_ptr[i+1] - row_ptr[i]) computed on the
+ * device and written to *max_row_len (host).  Synchronises `stream`.  Uses a
+ * 4-byte stream-ordered device allocation.
+ */
+int spmm_csr_max_row_length(int m, const int *row_ptr, long long *max_row_len, void *stream);
 
 /*
  * C = A B in float32 (vals, B, C all float32), the signature of the paper's
@@ -164,6 +191,43 @@ int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, c
  */
 int spmm_debug_bounded_wait(int *d_status, long long limit_ns, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Backward of C = A B (not in the paper, which names SpMM_T only as future
+ * work in Section 6): dB = A^T dC through spmm_csr_ex on A^T, and
+ * dvals = SDDMM(dC, B) on A's pattern.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of workspace spmm_csr_transpose needs (0 for invalid sizes). */
+size_t spmm_csr_transpose_workspace_size(int m, int k, long long nnz);
+
+/*
+ * A^T in CSR form by a stable sort of the nonzeros on their column index:
+ * row c of A^T lists the nonzeros of column c of A in increasing original
+ * position p; col_ind_t[q] is the row of A holding that nonzero and perm[q]
+ * its position p, so vals_t[q] = vals[perm[q]] (spmm_gather_values).
+ * row_ptr_t has k + 1 entries; col_ind_t and perm have nnz entries.  The
+ * result is deterministic.  workspace as in spmm_csr_ex (NULL with 0 bytes
+ * = stream-ordered allocation).
+ */
+int spmm_csr_transpose(int m, int k, long long nnz, const int *row_ptr, const int *col_ind, int *row_ptr_t,
+                       int *col_ind_t, int *perm, void *workspace, size_t workspace_bytes, void *stream);
+
+/* out[q] = vals[perm[q]] for q < nnz (vals_type: any spmm_dtype_t). */
+int spmm_gather_values(long long nnz, const int *perm, const void *vals, int vals_type, void *out, void *stream);
+
+/*
+ * Sampled dense-dense product on A's pattern:
+ * out[p] = sum_j dC[i][j] * B[col_ind[p]][j] for every nonzero p of row i,
+ * the gradient of <dC, A B> with respect to the stored values.  dC is m x n
+ * (leading dimension lddc), B is k x n (ldb); dC and B share one type;
+ * (dc/b type, out type) in {(f32,f32), (bf16,bf16), (bf16,f32), (f16,f16),
+ * (f16,f32)}.  Float32 accumulation.  Work is split into equal runs of
+ * consecutive nonzeros (Section 4 item 2(a), nonzero split).
+ */
+int sddmm_csr(int m, int k, int n, long long nnz, const int *row_ptr, const int *col_ind, const void *dC,
+              int dc_type, long long lddc, const void *B, int b_type, long long ldb, void *out, int out_type,
+              void *stream);
+
 /*
  * Allocation-free form of spmm_csr_ex.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at call
@@ -186,6 +250,8 @@ int spmm_debug_bounded_wait(int *d_status, long long limit_ns, void *stream);
  * it needs to start at zero, but calls that overlap on the GPU (on different
  * streams, or from several threads) race on it: serialise them.
  * nnz = -1 reads row_ptr[m] back (a 4-byte copy that synchronises `stream`).
+ * alg SPMM_ALG_AUTO_GB300 is not accepted here (measuring the longest row
+ * allocates); use SPMM_ALG_AUTO, SPMM_ALG_ROW_SPLIT or SPMM_ALG_MERGE.
  */
 int spmm_csr_noalloc(int m, int k, int n, long long nnz, const int *row_ptr, const int *col_ind,
                      const void *vals, int vals_type, const void *B, int b_type, long long ldb, void *C,

@@ -169,10 +169,13 @@ def abs_bound(row_ptr, col_ind, vals, B) -> np.ndarray:
     return abs_bound_rows(np.arange(m), row_ptr, col_ind, vals, B)
 
 
-def normalized_error(C, C_ref, D) -> float:
+def normalized_error(C, C_ref, D, abs_floor: float = 0.0) -> float:
     """Acceptance metric max |C - C_ref| / D over all elements.  Where D == 0 the
     product has no nonzero terms and C must be exactly zero there; a violation
-    returns +inf."""
+    returns +inf.  ``abs_floor`` is subtracted from each absolute difference
+    first: an output format with subnormals (IEEE binary16 below 2^-14) rounds
+    with an absolute error of up to half its subnormal spacing there, which no
+    relative bound covers."""
     C = np.asarray(C, dtype=np.float64)
     C_ref = np.asarray(C_ref, dtype=np.float64)
     D = np.asarray(D, dtype=np.float64)
@@ -183,7 +186,7 @@ def normalized_error(C, C_ref, D) -> float:
     zero = D == 0
     if np.any(C[zero] != 0.0):
         return float("inf")
-    err = np.abs(C - C_ref)
+    err = np.maximum(np.abs(C - C_ref) - abs_floor, 0.0)
     nz = ~zero
     return float((err[nz] / D[nz]).max()) if np.any(nz) else 0.0
 

@@ -21,13 +21,14 @@ import ctypes
 import os
 import threading
 
-ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE = 0, 1, 2
+ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300 = 0, 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
 OK = 0
 ERR_INVALID_VALUE, ERR_ALLOC, ERR_LAUNCH, ERR_BAD_CSR, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE = range(1, 9)
 PAPER_THRESHOLD = 9.35  # Section 5.4
 
-_ALG_NAMES = {"auto": ALG_AUTO, "row_split": ALG_ROW_SPLIT, "rowsplit": ALG_ROW_SPLIT, "merge": ALG_MERGE}
+_ALG_NAMES = {"auto": ALG_AUTO, "row_split": ALG_ROW_SPLIT, "rowsplit": ALG_ROW_SPLIT, "merge": ALG_MERGE,
+              "auto_gb300": ALG_AUTO_GB300}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspmm_gb300.so")
 _lock = threading.Lock()
@@ -44,7 +45,8 @@ class SpmmTuning(ctypes.Structure):
     """Mirror of spmm_tuning_t (zero fields = library's choice)."""
 
     _fields_ = [("lanes_per_row", ctypes.c_int), ("column_slabs", ctypes.c_int),
-                ("items_per_subwarp", ctypes.c_int), ("merge_threshold", ctypes.c_double)]
+                ("items_per_subwarp", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("merge_threshold", ctypes.c_double), ("max_row_len", ctypes.c_longlong)]
 
 
 _i, _ll, _vp, _sz, _d = ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double
@@ -54,6 +56,8 @@ _SIGNATURES = {
     "spmm_version": ([], _i),
     "spmm_launch_count": ([], _ll),
     "spmm_select_alg": ([_i, _ll, _d], _i),
+    "spmm_select_alg_gb300": ([_i, _ll, _ll, _i, _i], _i),
+    "spmm_csr_max_row_length": ([_i, _vp, ctypes.POINTER(_ll), _vp], _i),
     "spmm_csr": ([_i, _i, _i, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _vp], _i),
     "spmm_csr_ex": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _sz, _vp, _vp], _i),
     "spmm_csr_workspace_size": ([_i, _i, _i, _ll, _i, _i, _TP], _sz),
@@ -62,6 +66,10 @@ _SIGNATURES = {
     "spmm_debug_bounded_wait": ([_vp, _ll, _vp], _i),
     "spmm_csr_noalloc": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _vp], _i),
     "spmm_csr_static_scratch_bytes": ([], _sz),
+    "spmm_csr_transpose_workspace_size": ([_i, _i, _ll], _sz),
+    "spmm_csr_transpose": ([_i, _i, _ll, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "spmm_gather_values": ([_ll, _vp, _vp, _i, _vp, _vp], _i),
+    "sddmm_csr": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _vp], _i),
 }
 
 
@@ -113,6 +121,24 @@ def spmm_select_alg(m: int, nnz: int, threshold: float = 0.0) -> int:
     return load().spmm_select_alg(m, nnz, threshold)
 
 
+def spmm_select_alg_gb300(m: int, nnz: int, max_row_len: int, n: int, b_type: int = F32) -> int:
+    return load().spmm_select_alg_gb300(m, nnz, max_row_len, n, b_type)
+
+
+def spmm_csr_max_row_length(m, row_ptr, stream) -> tuple[int, int]:
+    """Returns (status, longest row)."""
+    out = ctypes.c_longlong(0)
+    st = load().spmm_csr_max_row_length(m, row_ptr, ctypes.byref(out), stream)
+    return st, out.value
+
+
+def max_row_length(row_ptr, stream=None) -> int:
+    _require_cuda(row_ptr)
+    st, v = spmm_csr_max_row_length(row_ptr.numel() - 1, row_ptr.data_ptr(), _stream_handle(stream))
+    _check(st, "spmm_csr_max_row_length")
+    return v
+
+
 def spmm_csr(m, k, n, row_ptr, col_ind, vals, B, ldb, C, ldc, alg, stream) -> int:
     return load().spmm_csr(m, k, n, row_ptr, col_ind, vals, B, ldb, C, ldc, alg, stream)
 
@@ -153,6 +179,24 @@ def spmm_csr_noalloc(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type,
 
 def spmm_csr_static_scratch_bytes() -> int:
     return load().spmm_csr_static_scratch_bytes()
+
+
+def spmm_csr_transpose_workspace_size(m, k, nnz) -> int:
+    return load().spmm_csr_transpose_workspace_size(m, k, nnz)
+
+
+def spmm_csr_transpose(m, k, nnz, row_ptr, col_ind, row_ptr_t, col_ind_t, perm, workspace, workspace_bytes,
+                       stream) -> int:
+    return load().spmm_csr_transpose(m, k, nnz, row_ptr, col_ind, row_ptr_t, col_ind_t, perm, workspace,
+                                     workspace_bytes, stream)
+
+
+def spmm_gather_values(nnz, perm, vals, vals_type, out, stream) -> int:
+    return load().spmm_gather_values(nnz, perm, vals, vals_type, out, stream)
+
+
+def sddmm_csr(m, k, n, nnz, row_ptr, col_ind, dC, dc_type, lddc, B, b_type, ldb, out, out_type, stream) -> int:
+    return load().sddmm_csr(m, k, n, nnz, row_ptr, col_ind, dC, dc_type, lddc, B, b_type, ldb, out, out_type, stream)
 
 
 def _tuning_ptr(t):
@@ -262,3 +306,47 @@ def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None
 def workspace_size(m, k, n, nnz, alg="auto", b_dtype=None, tuning=None) -> int:
     torch = _torch()
     return spmm_csr_workspace_size(m, k, n, nnz, alg_code(alg), dtype_code(b_dtype or torch.float32), tuning)
+
+
+def csr_transpose(row_ptr, col_ind, k: int, stream=None):
+    """A^T of a CSR A (k = columns of A): returns (row_ptr_t [k+1], col_ind_t, perm) int32 CUDA tensors."""
+    torch = _torch()
+    _require_cuda(row_ptr, col_ind)
+    m, nnz = row_ptr.numel() - 1, col_ind.numel()
+    dev = row_ptr.device
+    rpt = torch.empty(k + 1, dtype=torch.int32, device=dev)
+    cit = torch.empty(nnz, dtype=torch.int32, device=dev)
+    perm = torch.empty(nnz, dtype=torch.int32, device=dev)
+    _check(spmm_csr_transpose(m, k, nnz, row_ptr.data_ptr(), col_ind.data_ptr(), rpt.data_ptr(), cit.data_ptr(),
+                              perm.data_ptr(), None, 0, _stream_handle(stream)), "spmm_csr_transpose")
+    return rpt, cit, perm
+
+
+def gather_values(perm, vals, out=None, stream=None):
+    """out[q] = vals[perm[q]] on the device."""
+    torch = _torch()
+    _require_cuda(perm, vals)
+    out = torch.empty_like(vals) if out is None else out
+    _check(spmm_gather_values(perm.numel(), perm.data_ptr(), vals.data_ptr(), dtype_code(vals.dtype), out.data_ptr(),
+                              _stream_handle(stream)), "spmm_gather_values")
+    return out
+
+
+def sddmm(row_ptr, col_ind, dC, B, out=None, out_dtype=None, stream=None):
+    """out[p] = <dC[row(p), :], B[col_ind[p], :]> for every stored entry of the CSR pattern."""
+    torch = _torch()
+    _require_cuda(row_ptr, col_ind, dC, B, out)
+    if dC.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("dC and B must be row-major")
+    m, n = dC.shape
+    k = B.shape[0]
+    nnz = col_ind.numel()
+    if out is None:
+        out = torch.empty(nnz, dtype=out_dtype or dC.dtype, device=dC.device)
+    _check(sddmm_csr(m, k, n, nnz, row_ptr.data_ptr(), col_ind.data_ptr(), dC.data_ptr(), dtype_code(dC.dtype),
+                     dC.stride(0), B.data_ptr(), dtype_code(B.dtype), B.stride(0), out.data_ptr(),
+                     dtype_code(out.dtype), _stream_handle(stream)), "sddmm_csr")
+    return out
+
+
+from .autograd import CSRMatrix, SpMMFunction, spmm_autograd  # noqa: E402,F401

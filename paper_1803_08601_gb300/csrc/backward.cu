@@ -1,0 +1,411 @@
+// Operations of the backward pass of C = A B with respect to the stored
+// values of A and to B (the paper's SpMM_T, named as future work in
+// Section 6, plus the sampled dense-dense product):
+//   dB    = A^T dC      : spmm_csr_ex on A^T, built once by spmm_csr_transpose
+//   dvals = SDDMM(dC, B): dvals[p] = <dC[row(p), :], B[col(p), :]>
+//
+// CSR transpose: a stable sort of the nonzeros by column index (LSD radix
+// sort, 8 bits per pass, the original position as payload), so row c of A^T
+// lists the nonzeros of column c in increasing original position.  Every step
+// is deterministic; the permutation lets vals^T be refreshed with one gather
+// when the values change but the pattern does not.
+//
+// SDDMM: balanced by nonzero split (Section 4 item 2(a)): every lane group
+// takes an equal run of consecutive nonzeros and finds its first row by a
+// binary search on row_ptr, so a long row is shared by many groups.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "launch.cuh"
+
+namespace spmm {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanThreads = 1024;
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return SPMM_OK;
+    if (e == cudaErrorMemoryAllocation) return SPMM_ERR_ALLOC;
+    if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources || e == cudaErrorInvalidValue)
+        return SPMM_ERR_LAUNCH;
+    return SPMM_ERR_CUDA;
+}
+
+int launched(cudaError_t e) {
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return status_of(e);
+}
+
+int radix_passes(int k) {
+    int bits = 0;
+    while (bits < 31 && ((long long)(k > 0 ? k - 1 : 0) >> bits) > 0) ++bits;
+    const int p = (bits + 7) / 8;
+    return p < 1 ? 1 : p;
+}
+
+struct TransposeLayout {
+    int tiles;
+    size_t off_k0, off_k1, off_v, off_hist, total;
+};
+
+TransposeLayout transpose_layout(long long nnz) {
+    TransposeLayout L{};
+    L.tiles = (int)((nnz + kSortTile - 1) / kSortTile);
+    size_t off = 0;
+    L.off_k0 = off;
+    off = a256(off + (size_t)nnz * 4);
+    L.off_k1 = off;
+    off = a256(off + (size_t)nnz * 4);
+    L.off_v = off;
+    off = a256(off + (size_t)nnz * 4);
+    L.off_hist = off;
+    off = a256(off + (size_t)kRadix * (L.tiles > 0 ? L.tiles : 1) * 4);
+    L.total = off;
+    return L;
+}
+
+// Per-tile histogram of one 8-bit digit; hist is digit-major [256][tiles].
+__global__ void radix_hist_kernel(const int* __restrict__ keys, long long n, int shift, int tiles,
+                                  int* __restrict__ hist) {
+    __shared__ int cnt[kRadix];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+        const long long idx = base + i;
+        if (idx < n) atomicAdd(&cnt[(__ldg(keys + idx) >> shift) & (kRadix - 1)], 1);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// In-place exclusive prefix sum of data[0..len) by one CTA: each thread sums a
+// contiguous chunk, the chunk sums are scanned in shared memory, then each
+// thread rewrites its chunk.  Only used on radix histograms (256 x tiles).
+__global__ void exclusive_scan_kernel(int* __restrict__ data, long long len) {
+    __shared__ long long part[kScanThreads];
+    const long long per = (len + kScanThreads - 1) / kScanThreads;
+    const long long lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
+    long long s = 0;
+    for (long long i = lo; i < hi; ++i) s += data[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {  // Hillis-Steele inclusive scan
+        const long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (long long i = lo; i < hi; ++i) {
+        const int v = data[i];
+        data[i] = (int)run;
+        run += v;
+    }
+}
+
+// Stable scatter of one radix pass.  A tile is consumed in rounds of 256
+// consecutive elements, thread t holding element t of the round; inside a
+// warp the rank among equal digits comes from __match_any_sync, across warps
+// from per-warp digit counts in shared memory, across rounds from a running
+// per-digit base.  Element order is therefore kept among equal digits.
+// payload_in == nullptr means the payload is the element's own index.
+__global__ void radix_scatter_kernel(const int* __restrict__ keys_in, const int* __restrict__ payload_in, long long n,
+                                     int shift, int tiles, const int* __restrict__ offsets, int* __restrict__ keys_out,
+                                     int* __restrict__ payload_out) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ int base[kRadix];
+    __shared__ int wcnt[kWarps][kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = offsets[(long long)tid * tiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long idx = (long long)blockIdx.x * kSortTile + (long long)r * kSortThreads + tid;
+        const bool valid = idx < n;
+        const int key = valid ? __ldg(keys_in + idx) : 0;
+        const int pay = valid ? (payload_in ? __ldg(payload_in + idx) : (int)idx) : 0;
+        const int d = valid ? (key >> shift) & (kRadix - 1) : kRadix + lane;  // invalid lanes match nobody
+        const unsigned peers = __match_any_sync(kFullMask, d);
+        const int rank = __popc(peers & lt_mask);
+        if (valid && lane == 31 - __clz(peers)) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = base[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            keys_out[pos] = key;
+            payload_out[pos] = pay;
+        }
+        __syncthreads();
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            tot += wcnt[w][tid];
+            wcnt[w][tid] = 0;
+        }
+        base[tid] += tot;
+        __syncthreads();
+    }
+}
+
+// row_ptr_t[c] = first position of column c in the sorted keys (lower bound).
+__global__ void transpose_rowptr_kernel(const int* __restrict__ sorted_keys, long long nnz, int k,
+                                        int* __restrict__ row_ptr_t) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > k) return;
+    long long lo = 0, hi = nnz;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (__ldg(sorted_keys + mid) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    row_ptr_t[c] = (int)lo;
+}
+
+// col_ind_t[q] = row of A holding nonzero perm[q] (last row whose start <= perm[q]).
+__global__ void transpose_rows_kernel(const int* __restrict__ row_ptr, int m, const int* __restrict__ perm,
+                                      long long nnz, int* __restrict__ col_ind_t) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    const int p = __ldg(perm + q);
+    int lo = 0, hi = m;  // find the largest r in [0, m) with row_ptr[r] <= p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(row_ptr + mid) <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    col_ind_t[q] = lo;
+}
+
+template <typename T>
+__global__ void gather_values_kernel(const int* __restrict__ perm, long long nnz, const T* __restrict__ vals,
+                                     T* __restrict__ out) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x)
+        out[q] = vals[__ldg(perm + q)];
+}
+
+// ------------------------------------------------------------------------------------- SDDMM
+
+struct SddmmArgs {
+    int m, n;
+    long long nnz;
+    const int* row_ptr;
+    const int* col_ind;
+    const void* dC;
+    long long lddc;
+    const void* B;
+    long long ldb;
+    void* out;
+    int chunk;  // nonzeros per lane group
+};
+
+// One lane group of W lanes per run of `chunk` consecutive nonzeros; each lane
+// owns the columns chunk j = sl, sl + W, ... (VEC elements each) of both rows;
+// kUnroll nonzeros are processed together and their partial dot products are
+// reduced across the group with xor shuffles.
+template <typename TD, typename TO, int VEC, int W>
+__global__ void __launch_bounds__(kThreads) sddmm_kernel(SddmmArgs a) {
+    constexpr int U = kUnroll;
+    const int lane = threadIdx.x & 31, sl = lane & (W - 1);
+    const long long g = ((long long)blockIdx.x * kThreads + threadIdx.x) / W;
+    const long long p0 = g * a.chunk;
+    const long long p1 = p0 + a.chunk < a.nnz ? p0 + a.chunk : a.nnz;
+    const TD* __restrict__ dC = static_cast<const TD*>(a.dC);
+    const TD* __restrict__ B = static_cast<const TD*>(a.B);
+    const int nchunks = (a.n + VEC - 1) / VEC;
+    int row = 0, row_end = 0;
+    if (p0 < p1) {  // last row whose start is <= p0
+        int lo = 0, hi = a.m;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.row_ptr + mid) <= p0) lo = mid;
+            else hi = mid - 1;
+        }
+        row = lo;
+        row_end = __ldg(a.row_ptr + row + 1);
+    }
+    const int nb = p0 < p1 ? (int)((p1 - p0 + U - 1) / U) : 0;
+    const int nb_max = __reduce_max_sync(kFullMask, nb);
+    for (int b = 0; b < nb_max; ++b) {
+        float part[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long p = p0 + (long long)b * U + u;
+            part[u] = 0.0f;
+            if (p < p1) {
+                while (p >= row_end) row_end = __ldg(a.row_ptr + (++row) + 1);
+                const TD* brow = B + (long long)__ldg(a.col_ind + p) * a.ldb;
+                const TD* drow = dC + (long long)row * a.lddc;
+                for (int j = sl; j < nchunks; j += W) {
+                    const Raw<TD, VEC> x = load_raw<TD, VEC>(brow + (long long)j * VEC);
+                    float y[VEC];
+                    load_vec<TD, VEC>(drow + (long long)j * VEC, y);
+                    float t[VEC];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) t[e] = 0.0f;
+                    fma_raw<TD, VEC>(t, 1.0f, x);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) part[u] = fmaf(t[e], y[e], part[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(kFullMask, part[u], off, W);
+        if (sl == 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long p = p0 + (long long)b * U + u;
+                if (p < p1) static_cast<TO*>(a.out)[p] = Elem<TO>::from_f(part[u]);
+            }
+        }
+    }
+}
+
+template <typename TD, typename TO, int VEC>
+cudaError_t sddmm_launch_vec(const SddmmArgs& a, int W, long long groups, cudaStream_t st) {
+    const long long blocks = (groups * W + kThreads - 1) / kThreads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    switch (W) {
+        case 1: sddmm_kernel<TD, TO, VEC, 1><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+        case 2: sddmm_kernel<TD, TO, VEC, 2><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+        case 4: sddmm_kernel<TD, TO, VEC, 4><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+        case 8: sddmm_kernel<TD, TO, VEC, 8><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+        case 16: sddmm_kernel<TD, TO, VEC, 16><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+        default: sddmm_kernel<TD, TO, VEC, 32><<<(unsigned)blocks, kThreads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename TD, typename TO>
+int sddmm_run(const SddmmArgs& a0, cudaStream_t st) {
+    SddmmArgs a = a0;
+    constexpr int V = Elem<TD>::kVec;
+    const bool vec_ok = a.n % V == 0 && a.lddc % V == 0 && a.ldb % V == 0 && ((uintptr_t)a.dC % 16) == 0 &&
+                        ((uintptr_t)a.B % 16) == 0;
+    const int vec = vec_ok ? V : 1;
+    const long long nchunks = ((long long)a.n + vec - 1) / vec;
+    int W = 1;
+    while (W < nchunks && W < 32) W <<= 1;
+    a.chunk = 32;
+    const long long groups = (a.nnz + a.chunk - 1) / a.chunk;
+    const cudaError_t e = vec_ok ? sddmm_launch_vec<TD, TO, V>(a, W, groups, st) : sddmm_launch_vec<TD, TO, 1>(a, W, groups, st);
+    return launched(e);
+}
+
+}  // namespace
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" {
+
+size_t spmm_csr_transpose_workspace_size(int m, int k, long long nnz) {
+    if (m < 0 || k < 0 || nnz < 0) return 0;
+    return transpose_layout(nnz).total;
+}
+
+int spmm_csr_transpose(int m, int k, long long nnz, const int* row_ptr, const int* col_ind, int* row_ptr_t,
+                       int* col_ind_t, int* perm, void* workspace, size_t workspace_bytes, void* stream) {
+    if (m < 0 || k < 0 || nnz < 0 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
+    if (!row_ptr_t || (nnz > 0 && (!row_ptr || !col_ind || !col_ind_t || !perm))) return SPMM_ERR_INVALID_VALUE;
+    if (nnz > 0 && m == 0) return SPMM_ERR_INVALID_VALUE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const TransposeLayout L = transpose_layout(nnz);
+    if (nnz == 0) {
+        const cudaError_t e = cudaMemsetAsync(row_ptr_t, 0, (size_t)(k + 1) * 4, s);
+        return status_of(e);
+    }
+    bool own = false;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    if (!ws) {
+        if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, L.total, s) != cudaSuccess) return SPMM_ERR_ALLOC;
+        ws = static_cast<unsigned char*>(p);
+        own = true;
+    } else if (workspace_bytes < L.total) {
+        return SPMM_ERR_WORKSPACE;
+    }
+    int* kbuf[2] = {reinterpret_cast<int*>(ws + L.off_k0), reinterpret_cast<int*>(ws + L.off_k1)};
+    int* vtmp = reinterpret_cast<int*>(ws + L.off_v);
+    int* hist = reinterpret_cast<int*>(ws + L.off_hist);
+    const int passes = radix_passes(k);
+    const int* kin = col_ind;
+    const int* vin = nullptr;  // payload of the first pass: the element index
+    int st = SPMM_OK;
+    for (int pass = 0; pass < passes && st == SPMM_OK; ++pass) {
+        const int shift = 8 * pass;
+        int* kout = kbuf[pass & 1];
+        int* vout = ((passes - 1 - pass) % 2 == 0) ? perm : vtmp;  // the last pass lands in perm
+        radix_hist_kernel<<<L.tiles, kSortThreads, 0, s>>>(kin, nnz, shift, L.tiles, hist);
+        st = launched(cudaGetLastError());
+        if (st != SPMM_OK) break;
+        exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(hist, (long long)kRadix * L.tiles);
+        st = launched(cudaGetLastError());
+        if (st != SPMM_OK) break;
+        radix_scatter_kernel<<<L.tiles, kSortThreads, 0, s>>>(kin, vin, nnz, shift, L.tiles, hist, kout, vout);
+        st = launched(cudaGetLastError());
+        kin = kout;
+        vin = vout;
+    }
+    if (st == SPMM_OK) {
+        transpose_rowptr_kernel<<<(unsigned)(((long long)k + 1 + 255) / 256), 256, 0, s>>>(kin, nnz, k, row_ptr_t);
+        st = launched(cudaGetLastError());
+    }
+    if (st == SPMM_OK) {
+        transpose_rows_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(row_ptr, m, perm, nnz, col_ind_t);
+        st = launched(cudaGetLastError());
+    }
+    if (own) {
+        const cudaError_t e = cudaFreeAsync(ws, s);
+        if (st == SPMM_OK && e != cudaSuccess) st = status_of(e);
+    }
+    return st;
+}
+
+int spmm_gather_values(long long nnz, const int* perm, const void* vals, int vals_type, void* out, void* stream) {
+    if (nnz < 0 || (nnz > 0 && (!perm || !vals || !out))) return SPMM_ERR_INVALID_VALUE;
+    if (vals_type != SPMM_F32 && vals_type != SPMM_BF16 && vals_type != SPMM_F16) return SPMM_ERR_UNSUPPORTED;
+    if (nnz == 0) return SPMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)std::min<long long>((nnz + 255) / 256, 152LL * 16);
+    if (vals_type == SPMM_F32)
+        gather_values_kernel<float><<<blocks, 256, 0, s>>>(perm, nnz, (const float*)vals, (float*)out);
+    else
+        gather_values_kernel<unsigned short><<<blocks, 256, 0, s>>>(perm, nnz, (const unsigned short*)vals,
+                                                                     (unsigned short*)out);
+    return launched(cudaGetLastError());
+}
+
+int sddmm_csr(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* dC, int dc_type,
+              long long lddc, const void* B, int b_type, long long ldb, void* out, int out_type, void* stream) {
+    if (m < 0 || k < 0 || n < 0 || nnz < 0 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
+    if (nnz == 0) return SPMM_OK;
+    if (!row_ptr || !col_ind || !out || m == 0 || k == 0) return SPMM_ERR_INVALID_VALUE;
+    if (n > 0 && (!dC || !B || lddc < n || ldb < n)) return SPMM_ERR_INVALID_VALUE;
+    if (dc_type != b_type) return SPMM_ERR_UNSUPPORTED;
+    SddmmArgs a{m, n, nnz, row_ptr, col_ind, dC, lddc, B, ldb, out, 32};
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {  // empty dot products
+        const int es = out_type == SPMM_F32 ? 4 : 2;
+        return status_of(cudaMemsetAsync(out, 0, (size_t)nnz * es, s));
+    }
+    if (b_type == SPMM_F32 && out_type == SPMM_F32) return sddmm_run<float, float>(a, s);
+    if (b_type == SPMM_BF16 && out_type == SPMM_BF16) return sddmm_run<__nv_bfloat16, __nv_bfloat16>(a, s);
+    if (b_type == SPMM_BF16 && out_type == SPMM_F32) return sddmm_run<__nv_bfloat16, float>(a, s);
+    if (b_type == SPMM_F16 && out_type == SPMM_F16) return sddmm_run<__half, __half>(a, s);
+    if (b_type == SPMM_F16 && out_type == SPMM_F32) return sddmm_run<__half, float>(a, s);
+    return SPMM_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

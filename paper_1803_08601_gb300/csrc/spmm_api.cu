@@ -2,6 +2,7 @@
 // heuristic, launch-shape selection, merge workspace layout, and dispatch to
 // the per-dtype launchers.
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -97,6 +98,15 @@ int resolve_alg(int alg, int m, long long nnz, const spmm_tuning_t* t) {
     return spmm_select_alg(m, nnz, threshold_of(t));
 }
 
+// Longest row by a grid-stride max reduction over row_ptr differences.
+__global__ void row_length_max_kernel(const int* __restrict__ row_ptr, int m, int* __restrict__ out) {
+    int best = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        best = max(best, __ldg(row_ptr + i + 1) - __ldg(row_ptr + i));
+    best = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
+}
+
 // Launch shape for a given access width.  The lane group of a row covers
 // W * vec columns; W is the smallest power of two whose group spans the
 // columns of one slab.
@@ -188,7 +198,7 @@ int cuda_status(cudaError_t e) {
 int check_args(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
                const void* B, long long ldb, const void* C, long long ldc, int alg) {
     if (m < 0 || k < 0 || n < 0 || nnz < -1 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
-    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_MERGE) return SPMM_ERR_INVALID_VALUE;
+    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_AUTO_GB300) return SPMM_ERR_INVALID_VALUE;
     if (m > 0 && n > 0) {
         if (!row_ptr || !C) return SPMM_ERR_INVALID_VALUE;
         if (ldc < n) return SPMM_ERR_INVALID_VALUE;
@@ -242,8 +252,44 @@ int spmm_select_alg(int m, long long nnz, double threshold) {
     return d < threshold ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT;
 }
 
+int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type) {
+    if (m <= 0) return SPMM_ALG_ROW_SPLIT;
+    if (max_row_len > 1024 && max_row_len * 4096 > nnz) return SPMM_ALG_MERGE;  // Type 1 guard
+    const double d = (double)nnz / (double)m;
+    const long long row_bytes = (long long)n * (dtype_size(b_type) ? dtype_size(b_type) : 4);
+    if (row_bytes >= 64 && d < 5.0) return SPMM_ALG_MERGE;
+    return SPMM_ALG_ROW_SPLIT;
+}
+
+int spmm_csr_max_row_length(int m, const int* row_ptr, long long* max_row_len, void* stream) {
+    if (m < 0 || !max_row_len || (m > 0 && !row_ptr)) return SPMM_ERR_INVALID_VALUE;
+    *max_row_len = 0;
+    if (m == 0) return SPMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, sizeof(int), s) != cudaSuccess) return SPMM_ERR_ALLOC;
+    int* d = static_cast<int*>(p);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    const int threads = 256;
+    const int blocks = (int)std::min<long long>(((long long)m + threads - 1) / threads, 4 * 152);
+    if (e == cudaSuccess) {
+        row_length_max_kernel<<<blocks, threads, 0, s>>>(row_ptr, m, d);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return cuda_status(e);
+    *max_row_len = v;
+    return SPMM_OK;
+}
+
 size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int b_type, const spmm_tuning_t* tuning) {
     if (m < 0 || k < 0 || n < 0 || nnz < 0 || dtype_size(b_type) == 0) return 0;
+    if (alg == SPMM_ALG_AUTO_GB300) alg = SPMM_ALG_MERGE;  // the choice may need the longest row: size for merge
     if (resolve_alg(alg, m, nnz, tuning) != SPMM_ALG_MERGE || m == 0 || n == 0) return 0;
     // the access width depends on pointer alignment, unknown here: size for both widths
     size_t best = 0;
@@ -286,6 +332,14 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
     }
     Shape shape;
     if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, tuning, &shape)) return SPMM_ERR_INVALID_VALUE;
+    if (alg == SPMM_ALG_AUTO_GB300) {
+        long long lmax = tuning ? tuning->max_row_len : 0;
+        if (lmax <= 0) {
+            st = spmm_csr_max_row_length(m, row_ptr, &lmax, stream);
+            if (st != SPMM_OK) return st;
+        }
+        alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
+    }
     const int a = resolve_alg(alg, m, nnz, tuning);
     if (a == SPMM_ALG_ROW_SPLIT) {
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};

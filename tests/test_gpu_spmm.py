@@ -9,7 +9,7 @@ from spmm_cases import FP32_TOL, STRUCTURES, check, csr_arrays, structure
 
 pytestmark = pytest.mark.gpu
 
-ALGS = ["row_split", "merge", "auto"]
+ALGS = ["row_split", "merge", "auto", "auto_gb300"]
 
 
 def to_dev(torch, *arrays):
@@ -134,6 +134,21 @@ def test_explicit_workspace_and_status(gpu_lib):
     with pytest.raises(pkg.SpMMError) as e:
         run(pkg, torch, rp, ci, v, B, "merge", workspace=ws[: size // 4])
     assert e.value.status == pkg.ERR_WORKSPACE
+
+
+def test_gb300_selector_picks_merge_for_heavy_tail(gpu_lib):
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("giant_row")
+    d_rp = torch.from_numpy(rp).cuda()
+    assert pkg.max_row_length(d_rp) == int(np.diff(rp).max())
+    assert pkg.spmm_select_alg_gb300(len(rp) - 1, int(rp[-1]), pkg.max_row_length(d_rp), 64) == pkg.ALG_MERGE
+    c0 = pkg.spmm_launch_count()
+    B = gen.normal_matrix(k, 64, 3)
+    C = run(pkg, torch, rp, ci, v, B, "auto_gb300")  # measures the longest row itself: 1 + 3 launches
+    assert pkg.spmm_launch_count() - c0 == 4
+    check(C.cpu().numpy(), rp, ci, v, B)
 
 
 def test_launch_counts(gpu_lib):

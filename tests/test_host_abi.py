@@ -52,6 +52,20 @@ def test_heuristic_matches_oracle(lib, m, nnz):
     assert pkg.spmm_select_alg(m, nnz, pkg.PAPER_THRESHOLD) == oracle.select_alg(m, nnz)
 
 
+def test_gb300_selector(lib):
+    F, H = pkg.F32, pkg.BF16
+    # Type 1 guard: a very long row sends a matrix with a long mean row length to merge
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 64, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 1_000, 64, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(4096, 65_536, 16, 64, F) == pkg.ALG_ROW_SPLIT
+    # recalibrated mean-length rule: short rows go to merge only with rows of B of >= 64 bytes
+    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 64, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 8, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 32, H) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(10**6, 6 * 10**6, 6, 64, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(0, 0, 0, 64, F) == pkg.ALG_ROW_SPLIT
+
+
 def test_heuristic_custom_threshold(lib):
     assert pkg.spmm_select_alg(100, 1500, 20.0) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg(100, 1500, 10.0) == pkg.ALG_ROW_SPLIT

@@ -140,6 +140,10 @@ def test_normalized_error_semantics():
     C3 = ref.copy()
     C3[1, 0] = np.nan
     assert oracle.normalized_error(C3, ref, D) == float("inf")
+    # an absolute floor forgives differences up to it, and no more
+    assert oracle.normalized_error(C, ref, D, abs_floor=1e-3) == pytest.approx(0.75e-3)
+    assert oracle.normalized_error(C, ref, D, abs_floor=1.0) == 0.0
+    assert oracle.normalized_error(C2, ref, D, abs_floor=1.0) == float("inf")
 
 
 def test_thread_count_does_not_change_results():
