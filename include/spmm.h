@@ -228,6 +228,76 @@ int sddmm_csr(int m, int k, int n, long long nnz, const int *row_ptr, const int 
               int dc_type, long long lddc, const void *B, int b_type, long long ldb, void *out, int out_type,
               void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form (not in the paper): many independent float32 products
+ * C_b = A_b B_b of uneven sizes in one persistent kernel launch plus one
+ * fix-up launch, replayable as a CUDA graph.  Each matrix runs one of the
+ * paper's two families: row split contributes chunks of consecutive rows,
+ * merge based contributes merge-path tiles (Section 4.2) whose partition is
+ * computed once, when the plan is made.
+ * ---------------------------------------------------------------------- */
+
+/* One product of a batch.  Device pointers, caller-owned, float32; n, ldb,
+   ldc multiples of 4 and B, C 16-byte aligned (16-byte accesses only). */
+typedef struct {
+    int m, k, n;
+    long long nnz; /* host copy of row_ptr[m] */
+    const int *row_ptr;
+    const int *col_ind;
+    const float *vals;
+    const float *B;
+    long long ldb;
+    float *C;
+    long long ldc;
+} spmm_batch_matrix_t;
+
+typedef struct spmm_batched_plan spmm_batched_plan_t; /* opaque */
+
+typedef enum {
+    SPMM_BATCHED_MODEL = 0,     /* per matrix: spmm_select_alg_gb300 (longest rows read at plan time) */
+    SPMM_BATCHED_AUTOTUNE = 1,  /* per matrix: the autotuner's pick for its shape bucket            */
+    SPMM_BATCHED_ROW_SPLIT = 2, /* every matrix row split                                            */
+    SPMM_BATCHED_MERGE = 3      /* every matrix merge based                                          */
+} spmm_batched_policy_t;
+
+/*
+ * Make a plan for `count` products (host array of descriptors; the pointed-to
+ * device arrays must stay valid and keep their sparsity patterns while the
+ * plan is used; values of vals and B may change between runs).  The plan owns
+ * one device allocation (work list, merge partitions, carry buffers) and
+ * synchronises `stream` once.  SPMM_BATCHED_AUTOTUNE times, for every shape
+ * bucket (n, floor(log2 m), mean row length class) not yet in the process-wide
+ * cache, row split and merge based with three tile sizes on up to 8 of the
+ * plan's matrices of that bucket, and keeps the fastest.
+ */
+int spmm_batched_plan_create(int count, const spmm_batch_matrix_t *mats, int policy, void *stream,
+                             spmm_batched_plan_t **plan);
+
+/* Enqueue the batch: the persistent kernel and the fix-up (two launches). */
+int spmm_batched_run(const spmm_batched_plan_t *plan, void *stream);
+
+/* Capture spmm_batched_run into a CUDA graph owned by the plan (replaces a
+   previous one).  Capture happens on a private stream (the legacy default
+   stream cannot be captured); `stream` is unused. */
+int spmm_batched_capture_graph(spmm_batched_plan_t *plan, void *stream);
+
+/* Launch the captured graph on `stream`. */
+int spmm_batched_launch_graph(const spmm_batched_plan_t *plan, void *stream);
+
+/* Baseline: the same per-matrix choices as one spmm_csr_ex call per matrix
+   (partition, compute and fix-up launches for merge matrices). */
+int spmm_batched_run_unfused(const spmm_batched_plan_t *plan, void *stream);
+
+/* Per-matrix algorithm chosen (host array of count ints, may be NULL), work
+   items of the persistent kernel and merge tiles (either may be NULL). */
+int spmm_batched_plan_query(const spmm_batched_plan_t *plan, int *algs, long long *num_items, int *num_tiles);
+
+int spmm_batched_plan_destroy(spmm_batched_plan_t *plan);
+
+/* The autotuner's process-wide cache of per-bucket picks. */
+long long spmm_autotune_cache_entries(void);
+int spmm_autotune_cache_clear(void);
+
 /*
  * Allocation-free form of spmm_csr_ex.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at call

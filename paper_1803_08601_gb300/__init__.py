@@ -350,3 +350,129 @@ def sddmm(row_ptr, col_ind, dC, B, out=None, out_dtype=None, stream=None):
 
 
 from .autograd import CSRMatrix, SpMMFunction, spmm_autograd  # noqa: E402,F401
+
+
+# ----------------------------------------------------------------------------- batched form
+
+BATCHED_MODEL, BATCHED_AUTOTUNE, BATCHED_ROW_SPLIT, BATCHED_MERGE = 0, 1, 2, 3
+
+
+class SpmmBatchMatrix(ctypes.Structure):
+    """Mirror of spmm_batch_matrix_t."""
+
+    _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("n", ctypes.c_int), ("nnz", ctypes.c_longlong),
+                ("row_ptr", ctypes.c_void_p), ("col_ind", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_longlong), ("C", ctypes.c_void_p), ("ldc", ctypes.c_longlong)]
+
+
+_BSIG = {
+    "spmm_batched_plan_create": ([_i, ctypes.POINTER(SpmmBatchMatrix), _i, _vp, ctypes.POINTER(_vp)], _i),
+    "spmm_batched_run": ([_vp, _vp], _i),
+    "spmm_batched_capture_graph": ([_vp, _vp], _i),
+    "spmm_batched_launch_graph": ([_vp, _vp], _i),
+    "spmm_batched_run_unfused": ([_vp, _vp], _i),
+    "spmm_batched_plan_query": ([_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(_i)], _i),
+    "spmm_batched_plan_destroy": ([_vp], _i),
+    "spmm_autotune_cache_entries": ([], _ll),
+    "spmm_autotune_cache_clear": ([], _i),
+}
+_SIGNATURES.update(_BSIG)
+
+
+def _bind_batched():
+    lib = load()
+    for name, (args, res) in _BSIG.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def spmm_batched_plan_create(count, mats, policy, stream, plan_out) -> int:
+    return _bind_batched().spmm_batched_plan_create(count, mats, policy, stream, plan_out)
+
+
+def spmm_batched_run(plan, stream) -> int:
+    return _bind_batched().spmm_batched_run(plan, stream)
+
+
+def spmm_batched_capture_graph(plan, stream) -> int:
+    return _bind_batched().spmm_batched_capture_graph(plan, stream)
+
+
+def spmm_batched_launch_graph(plan, stream) -> int:
+    return _bind_batched().spmm_batched_launch_graph(plan, stream)
+
+
+def spmm_batched_run_unfused(plan, stream) -> int:
+    return _bind_batched().spmm_batched_run_unfused(plan, stream)
+
+
+def spmm_batched_plan_query(plan, algs, num_items, num_tiles) -> int:
+    return _bind_batched().spmm_batched_plan_query(plan, algs, num_items, num_tiles)
+
+
+def spmm_batched_plan_destroy(plan) -> int:
+    return _bind_batched().spmm_batched_plan_destroy(plan)
+
+
+def spmm_autotune_cache_entries() -> int:
+    return _bind_batched().spmm_autotune_cache_entries()
+
+
+def spmm_autotune_cache_clear() -> int:
+    return _bind_batched().spmm_autotune_cache_clear()
+
+
+class BatchedPlan:
+    """A plan over lists of CUDA tensors: row_ptrs, col_inds, vals (float32), Bs [k, n], Cs [m, n].
+    The tensors must outlive the plan."""
+
+    def __init__(self, row_ptrs, col_inds, vals, Bs, Cs, policy=BATCHED_MODEL, nnzs=None, stream=None):
+        count = len(row_ptrs)
+        arr = (SpmmBatchMatrix * max(count, 1))()
+        for i in range(count):
+            rp, ci, v, B, C = row_ptrs[i], col_inds[i], vals[i], Bs[i], Cs[i]
+            _require_cuda(rp, ci, v, B, C)
+            m, (k, n) = rp.numel() - 1, B.shape
+            nnz = int(nnzs[i]) if nnzs is not None else ci.numel()
+            arr[i] = SpmmBatchMatrix(m, k, n, nnz, rp.data_ptr(), ci.data_ptr(), v.data_ptr(), B.data_ptr(),
+                                     B.stride(0), C.data_ptr(), C.stride(0))
+        self.count = count
+        self._keep = (row_ptrs, col_inds, vals, Bs, Cs)
+        h = ctypes.c_void_p()
+        _check(spmm_batched_plan_create(count, arr, policy, _stream_handle(stream), ctypes.byref(h)),
+               "spmm_batched_plan_create")
+        self.handle = h
+        self.has_graph = False
+
+    def run(self, stream=None):
+        _check(spmm_batched_run(self.handle, _stream_handle(stream)), "spmm_batched_run")
+
+    def capture_graph(self, stream=None):
+        _check(spmm_batched_capture_graph(self.handle, _stream_handle(stream)), "spmm_batched_capture_graph")
+        self.has_graph = True
+
+    def launch_graph(self, stream=None):
+        _check(spmm_batched_launch_graph(self.handle, _stream_handle(stream)), "spmm_batched_launch_graph")
+
+    def run_unfused(self, stream=None):
+        _check(spmm_batched_run_unfused(self.handle, _stream_handle(stream)), "spmm_batched_run_unfused")
+
+    def query(self):
+        algs = (ctypes.c_int * max(self.count, 1))()
+        items, tiles = ctypes.c_longlong(0), ctypes.c_int(0)
+        _check(spmm_batched_plan_query(self.handle, algs, ctypes.byref(items), ctypes.byref(tiles)),
+               "spmm_batched_plan_query")
+        return list(algs)[: self.count], items.value, tiles.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spmm_batched_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -43,17 +43,19 @@ struct RowSplitArgs {
 // run with the full mask; lanes past the end of their row load nothing
 // (Section 4.1 passes a dummy column index there; predication does the same
 // without the load).
+// One row per lane group: the lane group owning `row` (row >= a.m: nothing to
+// do, but the lanes still join the warp's shuffles) computes the `slab`-th
+// W * VEC columns of C[row, :].  Every lane of the warp must call this the
+// same number of times.
 template <typename TV, typename TB, typename TC, int VEC, int W>
-__global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
+__device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long row, int slab) {
     constexpr int U = kUnroll;
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
     constexpr int BS = W * CV;               // nonzeros per batch
     constexpr int G = BS / U;                // groups of U gathers per batch
-    constexpr int RPW = 32 / W;              // rows per warp
     const int lane = threadIdx.x & 31;
     const int sl = lane & (W - 1);
-    const long long row = (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + lane / W;
-    const long long col0 = (long long)blockIdx.y * (W * VEC) + (long long)sl * VEC;
+    const long long col0 = (long long)slab * (W * VEC) + (long long)sl * VEC;
     const bool col_ok = col0 < a.n;
     const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
     const TB* __restrict__ B = static_cast<const TB*>(a.B);
@@ -98,6 +100,14 @@ __global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
         }
     }
     if (row < a.m && col_ok) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc);
+}
+
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
+    constexpr int RPW = 32 / W;  // rows per warp
+    const long long row =
+        (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / W;
+    rowsplit_row<TV, TB, TC, VEC, W>(a, row, blockIdx.y);
 }
 
 // ============================================================================ merge path
