@@ -3,8 +3,13 @@
 Default workload: the 1M x 1M power-law CSR matrix (row lengths with density
 exponent 2, mean about 16, capped at 100,000, 1% empty rows) times row-major
 float32 B of widths n = 8, 32, 64, 128.  One step = C = A B for every width,
-each through the C ABI with the algorithm chosen by the Section 5.4 heuristic
-(``--alg`` overrides).  All inputs are synthetic and seeded (gen/).
+each through the C ABI with the algorithm chosen by the GB300 selector (the
+Section 5.4 mean-row-length rule recalibrated, plus a longest-row guard); the
+JSON line also reports the Section 5.4 rule's own pick and both families'
+times (``--alg`` overrides).  After the headline, the growth forms are
+measured: 16-bit storage (2M x 2M, n = 128), a GCN layer's forward and
+backward (500k nodes, n = 256) and a 2048-matrix batch in one graph-captured
+persistent launch.  All inputs are synthetic and seeded (gen/).
 
 Timing: inputs resident in HBM; L2 is flushed (a write of twice its size)
 before every step, outside the events; each call is bracketed by CUDA events on
@@ -48,6 +53,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--tuning", default=None, help='JSON spmm_tuning_t fields, e.g. {"column_slabs": 2}')
+    p.add_argument("--forms", default="precision,backward,batched",
+                   help="comma list of growth forms measured after the headline (empty: none)")
     return p.parse_args()
 
 
@@ -331,6 +338,12 @@ def main():
             line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
                                     "sample": f"{passes} pass(es) over {nrows} seeded random rows of the {label} "
                                               f"matrix, all n, {t:.1f} s"}
+        del d_B, d_C, ws
+        torch.cuda.empty_cache()
+        line["forms"] = {}
+        for form in [f for f in args.forms.split(",") if f]:
+            line["forms"][form] = FORMS[form](pkg, torch, flush, stream, args.steps)
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -382,6 +395,138 @@ def e2e(pkg, torch, a, ns, Bs, args, tuning):
     flops = sum(2.0 * a.nnz * n for n in ns)
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3, "api": "spmm_csr_host"}
+
+
+
+# ----------------------------------------------------------------------------- growth forms
+
+def _time(torch, fn, flush, stream, reps):
+    """Median device time (ms) of fn() over reps runs, L2 flushed before each."""
+    for _ in range(2):
+        fn()
+    ts = []
+    for _ in range(max(3, reps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(statistics.median(ts))
+
+
+def _norm_diff(torch, C, C_ref, D):
+    """max |C - C_ref| / D on the device (D = |A||B| from the library; where D == 0 both must be 0)."""
+    diff = (C.float() - C_ref.float()).abs()
+    nz = D > 0
+    bad_zero = bool((diff[~nz] > 0).any().item()) if (~nz).any() else False
+    return float("inf") if bad_zero else float((diff[nz] / D[nz]).max().item())
+
+
+def form_precision(pkg, torch, flush, stream, steps):
+    """2M x 2M, 32 nonzeros per row, n = 128: 16-bit storage vs the float32 plain kernel."""
+    a, Bf = gen.workload_precision()
+    dev = torch.device("cuda")
+    rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
+    v32, B32 = torch.from_numpy(a.vals).to(dev), torch.from_numpy(Bf).to(dev)
+    nnz, n = a.nnz, Bf.shape[1]
+    lmax = pkg.max_row_length(rp)
+    tun = {"max_row_len": lmax}
+    flops = 2.0 * nnz * n
+    out = {"workload": "uniform 2Mx2M, 32/row, n=128", "nnz": nnz}
+    C32 = pkg.spmm(rp, ci, v32, B32, alg="auto_gb300", nnz=nnz, tuning=tun)
+    D = pkg.spmm(rp, ci, v32.abs(), B32.abs(), alg="auto_gb300", nnz=nnz, tuning=tun)
+    t32 = _time(torch, lambda: pkg.spmm(rp, ci, v32, B32, alg="auto_gb300", out=C32, nnz=nnz, tuning=tun),
+                flush, stream, steps)
+    out["f32_plain"] = {"ms": t32, "gflops": flops / t32 / 1e6}
+    variants = {"bf16_vals_bf16_B_bf16_C": (torch.bfloat16, torch.bfloat16, torch.bfloat16),
+                "bf16_vals_bf16_B_f32_C": (torch.bfloat16, torch.bfloat16, torch.float32),
+                "bf16_vals_f16_B_f32_C": (torch.bfloat16, torch.float16, torch.float32),
+                "f16_vals_f16_B_f16_C": (torch.float16, torch.float16, torch.float16)}
+    for name, (tv, tb, tc) in variants.items():
+        v16, B16 = v32.to(tv), B32.to(tb)
+        C = pkg.spmm(rp, ci, v16, B16, alg="auto_gb300", out_dtype=tc, nnz=nnz, tuning=tun)
+        t = _time(torch, lambda: pkg.spmm(rp, ci, v16, B16, alg="auto_gb300", out=C, nnz=nnz, tuning=tun),
+                  flush, stream, steps)
+        out[name] = {"ms": t, "gflops": flops / t / 1e6, "speedup_vs_f32": t32 / t,
+                     "max_norm_diff_vs_f32_path": _norm_diff(torch, C, C32, D)}
+        del v16, B16, C
+    return out
+
+
+def form_backward(pkg, torch, flush, stream, steps):
+    """GCN layer (500k nodes, mean degree ~20, n = 256): forward, dX = A^T dY, dvals = SDDMM."""
+    a, X = gen.workload_gcn()
+    dev = torch.device("cuda")
+    rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
+    v, dX_in = torch.from_numpy(a.vals).to(dev), torch.from_numpy(X).to(dev)
+    dY = torch.randn(a.m, X.shape[1], device=dev, generator=torch.Generator(device=dev).manual_seed(1807))
+    A = pkg.CSRMatrix(rp, ci, (a.m, a.k))
+    nnz, n = a.nnz, X.shape[1]
+    flops = 2.0 * nnz * n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A.transpose_pattern()
+    torch.cuda.synchronize()
+    t_transpose = (time.perf_counter() - t0) * 1e3
+    rpt, cit, perm, lmax_t = A.transpose_pattern()
+    vt = pkg.gather_values(perm, v)
+    Y = A.spmm(v, dX_in)
+    dX = pkg.spmm(rpt, cit, vt, dY, alg="auto_gb300", nnz=nnz, tuning={"max_row_len": lmax_t})
+    dv = pkg.sddmm(rp, ci, dY, dX_in)
+    t_fwd = _time(torch, lambda: A.spmm(v, dX_in, out=Y), flush, stream, steps)
+    t_dx = _time(torch, lambda: (pkg.gather_values(perm, v, out=vt),
+                                 pkg.spmm(rpt, cit, vt, dY, alg="auto_gb300", out=dX, nnz=nnz,
+                                          tuning={"max_row_len": lmax_t})), flush, stream, steps)
+    t_sd = _time(torch, lambda: pkg.sddmm(rp, ci, dY, dX_in, out=dv), flush, stream, steps)
+    # the plain float32 kernel on the forward shape, fixed family (reference point of the form)
+    t_plain = _time(torch, lambda: A.spmm(v, dX_in, out=Y, alg=pkg.ALG_ROW_SPLIT), flush, stream, steps)
+    return {"workload": "Chung-Lu GCN 500k, n=256", "nnz": nnz, "mean_degree": a.info["mean_degree"],
+            "max_degree": a.info["max_degree"], "transpose_once_ms": t_transpose,
+            "forward": {"ms": t_fwd, "gflops": flops / t_fwd / 1e6},
+            "dX_AT_dY": {"ms": t_dx, "gflops": flops / t_dx / 1e6, "includes": "vals gather + SpMM on A^T"},
+            "dvals_sddmm": {"ms": t_sd, "gflops": flops / t_sd / 1e6},
+            "f32_plain_row_split_forward": {"ms": t_plain, "gflops": flops / t_plain / 1e6},
+            "fwd_bwd_step_ms": t_fwd + t_dx + t_sd,
+            "speedup_fwd_vs_f32_plain": t_plain / t_fwd}
+
+
+def form_batched(pkg, torch, flush, stream, steps):
+    """2048 CSR matrices of uneven sizes in one persistent graph-captured launch vs a loop of launches."""
+    s = gen.workload_batched()
+    dev = torch.device("cuda")
+    rps, cis, vs, Bs, Cs = [], [], [], [], []
+    g = torch.Generator(device=dev).manual_seed(gen.SEED_BASE + 5)
+    for i, (a, n) in enumerate(zip(s.mats, s.ns)):
+        rps.append(torch.from_numpy(a.row_ptr).to(dev))
+        cis.append(torch.from_numpy(a.col_ind).to(dev))
+        vs.append(torch.from_numpy(a.vals).to(dev))
+        Bs.append(torch.randn(a.k, n, device=dev, generator=g))
+        Cs.append(torch.empty((a.m, n), device=dev))
+    flops = sum(2.0 * a.nnz * n for a, n in zip(s.mats, s.ns))
+    out = {"workload": "2048 matrices, m log-uniform [64, 65536], Poisson rows lambda U[4,64], n in {32,64,128}",
+           "total_nnz": s.info["total_nnz"], "total_rows": s.info["total_rows"]}
+    for pol_name, pol in (("model", pkg.BATCHED_MODEL), ("autotune", pkg.BATCHED_AUTOTUNE)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = pkg.BatchedPlan(rps, cis, vs, Bs, Cs, policy=pol)
+        torch.cuda.synchronize()
+        t_plan = (time.perf_counter() - t0) * 1e3
+        plan.capture_graph()
+        algs, items, tiles = plan.query()
+        t_graph = _time(torch, plan.launch_graph, flush, stream, steps)
+        t_loop = _time(torch, plan.run_unfused, flush, stream, max(3, steps // 3))
+        out[pol_name] = {"plan_ms": t_plan, "work_items": items, "merge_tiles": tiles,
+                         "merge_matrices": int(sum(1 for x in algs if x == pkg.ALG_MERGE)),
+                         "graph": {"ms": t_graph, "gflops": flops / t_graph / 1e6},
+                         "loop_of_launches": {"ms": t_loop, "gflops": flops / t_loop / 1e6},
+                         "speedup_vs_loop": t_loop / t_graph}
+        plan.close()
+    return out
+
+
+FORMS = {"precision": form_precision, "backward": form_backward, "batched": form_batched}
 
 
 if __name__ == "__main__":
