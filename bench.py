@@ -83,6 +83,29 @@ def compulsory_bytes(m, nnz, k, n, s_v=4, s_b=4, s_c=4):
     return (m + 1) * 4 + nnz * (4 + s_v) + k * n * s_b + m * n * s_c
 
 
+def measured_traffic(kernel, label, ns):
+    """DRAM bytes (read + write) of the dominant kernel summed over the step's widths, from the
+    committed ncu capture in profiles/, or None when the kernel sources changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"{kernel}_power_law_1M_dram.json")
+    if label != "power_law_1Mx1M_mean16_cap1e5" or not os.path.exists(path):
+        return None, "no capture for this kernel and workload"
+    with open(path) as f:
+        cap = json.load(f)
+    h = hashlib.sha256()
+    for p in cap["sources"]:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != cap["sources_sha256"]:
+        return None, "kernel sources changed since the ncu capture"
+    if not all(str(n) in cap["per_n"] for n in ns):
+        return None, "capture lacks some widths"
+    t = sum(cap["per_n"][str(n)]["dram_read_bytes"] + cap["per_n"][str(n)]["dram_write_bytes"] for n in ns)
+    return t, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch per width, summed over the "
+               f"step's widths {ns} (profiles/{os.path.basename(path)}); same units as achieved x duration")
+
+
 def peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -308,8 +331,9 @@ def main():
     fam = max({alg_of[n] for n in ns}, key=lambda al: sum(mean_call[n] for n in ns if alg_of[n] == al))
     fam_ns = [n for n in ns if alg_of[n] == fam]
     achieved = sum(comp[n] for n in fam_ns) / (sum(mean_call[n] for n in fam_ns) * 1e-3) / 1e9
+    traffic, traffic_note = measured_traffic(dom_alg[fam], label, fam_ns)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom_alg[fam], "peak_source": peak_src,
+                "traffic": traffic, "traffic_note": traffic_note, "kernel": dom_alg[fam], "peak_source": peak_src,
                 "algorithmic_bytes": "compulsory: (m+1)*4 + nnz*8 + k*n*4 + m*n*4 per call, summed over n",
                 "per_n": {str(n): {"ms": mean_call[n], "gb_s": comp[n] / (mean_call[n] * 1e-3) / 1e9,
                                    "gflops": 2.0 * nnz * n / (mean_call[n] * 1e-3) / 1e9,

@@ -88,9 +88,10 @@ __device__ __forceinline__ void batched_tile(const MatDesc& d, int* carry_row_al
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) batched_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items,
-                                                           long long n_items, int* carry_row_all, int* head_row_all,
-                                                           int* status) {
+// Three CTAs per SM: caps the registers of the (inlined) worst-case variant at 80.
+__global__ void __launch_bounds__(kThreads, 3)
+    batched_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
+                   int* carry_row_all, int* head_row_all, int* status) {
     extern __shared__ __align__(128) unsigned char smem[];
     for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
         const Item item = items[it];
@@ -448,8 +449,14 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 if (g_tune_cache.count(kv.first)) continue;
             }
+            // a sample big enough that the timed kernel runs well above launch latency:
+            // matrices of the bucket until 4M rows + nonzeros (at most 64 matrices)
             std::vector<spmm_batch_matrix_t> sample;
-            for (size_t i = 0; i < kv.second.size() && sample.size() < 8; ++i) sample.push_back(v[kv.second[i]]);
+            long long work = 0;
+            for (size_t i = 0; i < kv.second.size() && sample.size() < 64 && work < (4LL << 20); ++i) {
+                sample.push_back(v[kv.second[i]]);
+                work += v[kv.second[i]].m + v[kv.second[i]].nnz;
+            }
             Choice best{SPMM_ALG_ROW_SPLIT, 0};
             float best_ms = time_candidate(sample, SPMM_ALG_ROW_SPLIT, 0, s);
             for (int sc : {0, -1, 1}) {

@@ -447,16 +447,18 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col_ind, (size_t)nnz * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, vals, (size_t)nnz * sv, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && k > 0 && nnz > 0)
-        e = cudaMemcpy2DAsync(d_B, (size_t)ldb_d * sb, B, (size_t)ldb * sb, (size_t)n * sb, (size_t)k,
-                              cudaMemcpyHostToDevice, s);
+        e = ldb == ldb_d ? cudaMemcpyAsync(d_B, B, (size_t)k * ldb_d * sb, cudaMemcpyHostToDevice, s)
+                         : cudaMemcpy2DAsync(d_B, (size_t)ldb_d * sb, B, (size_t)ldb * sb, (size_t)n * sb, (size_t)k,
+                                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         st = spmm_csr_ex(m, k, n, nnz, d_rp, d_col, d_val, vals_type, d_B, b_type, ldb_d, d_C, c_type, ldc_d, alg,
                          tuning, nullptr, 0, nullptr, stream);
     else
         st = cuda_status(e);
     if (st == SPMM_OK) {
-        e = cudaMemcpy2DAsync(C, (size_t)ldc * sc, d_C, (size_t)ldc_d * sc, (size_t)n * sc, (size_t)m,
-                              cudaMemcpyDeviceToHost, s);
+        e = ldc == ldc_d ? cudaMemcpyAsync(C, d_C, (size_t)m * ldc_d * sc, cudaMemcpyDeviceToHost, s)
+                         : cudaMemcpy2DAsync(C, (size_t)ldc * sc, d_C, (size_t)ldc_d * sc, (size_t)n * sc, (size_t)m,
+                                             cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) st = cuda_status(e);
     }
     e = cudaFreeAsync(mem, s);
