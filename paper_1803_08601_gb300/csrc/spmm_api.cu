@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "launch.cuh"
 
@@ -186,6 +187,41 @@ void clamp_tile(Shape* s, int sv) {
     while (s->ips > 4 && bytes(*s) > kMaxSmem) s->ips = s->ips * 3 / 4;
 }
 
+// Stream-ordered allocations of this library come from the device's default
+// memory pool.  Its default release threshold (0) hands freed memory back to
+// the driver at every synchronisation, which makes each call pay the full
+// mapping cost again; keep it cached instead (once per device, for this
+// process only).
+void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+// Two copy streams per device (host-to-device, device-to-host), created once.
+bool copy_streams(cudaStream_t* up, cudaStream_t* down) {
+    static std::mutex mu;
+    static cudaStream_t streams[64][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < 2; ++i)
+        if (!streams[dev][i] && cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking) != cudaSuccess)
+            return false;
+    *up = streams[dev][0];
+    *down = streams[dev][1];
+    return true;
+}
+
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SPMM_OK;
     if (e == cudaErrorMemoryAllocation) return SPMM_ERR_ALLOC;
@@ -356,6 +392,7 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
     if (!ws) {
         if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
         void* p = nullptr;
+        keep_pool_memory();
         const cudaError_t e = cudaMallocAsync(&p, lay.total, s);
         if (e != cudaSuccess) return SPMM_ERR_ALLOC;
         ws = static_cast<unsigned char*>(p);
@@ -428,12 +465,21 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
     if (!find_launchers(vals_type, b_type, c_type)) return SPMM_ERR_UNSUPPORTED;
     if (m == 0 || n == 0) return SPMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    // device copies: B and C packed with leading dimension n (rounded to 16 bytes for the vector path)
+    keep_pool_memory();
+    cudaStream_t up = nullptr, down = nullptr;
+    if (!copy_streams(&up, &down)) return SPMM_ERR_CUDA;
+    // Device copies: B and C packed with leading dimension n (rounded to 16 bytes for the vector path).
     const long long vb = 16 / sb, vc = 16 / sc;
     const long long ldb_d = (n + vb - 1) / vb * vb, ldc_d = (n + vc - 1) / vc * vc;
     const size_t b_rp = align256((size_t)(m + 1) * 4), b_col = align256((size_t)nnz * 4),
                  b_val = align256((size_t)nnz * sv), b_B = align256((size_t)k * ldb_d * sb),
                  b_C = align256((size_t)m * ldc_d * sc);
+    // Column slabs pipeline the full-duplex host link: while slab j is computed, slab j+1 of B
+    // is uploaded and slab j-1 of C downloaded.  A slab is at least 128 bytes of a row.
+    int slabs = (int)std::min<long long>(4, std::max<long long>(1, (long long)n * sb / 128));
+    long long w = (n + slabs - 1) / slabs;
+    w = (w + 15) / 16 * 16;  // whole 16-byte vectors for every element size
+    slabs = (int)((n + w - 1) / w);
     void* mem = nullptr;
     cudaError_t e = cudaMallocAsync(&mem, b_rp + b_col + b_val + b_B + b_C, s);
     if (e != cudaSuccess) return SPMM_ERR_ALLOC;
@@ -441,30 +487,57 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
     int* d_rp = reinterpret_cast<int*>(base);
     int* d_col = reinterpret_cast<int*>(base + b_rp);
     void* d_val = base + b_rp + b_col;
-    void* d_B = base + b_rp + b_col + b_val;
-    void* d_C = base + b_rp + b_col + b_val + b_B;
-    e = cudaMemcpyAsync(d_rp, row_ptr, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col_ind, (size_t)nnz * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, vals, (size_t)nnz * sv, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && k > 0 && nnz > 0)
-        e = ldb == ldb_d ? cudaMemcpyAsync(d_B, B, (size_t)k * ldb_d * sb, cudaMemcpyHostToDevice, s)
-                         : cudaMemcpy2DAsync(d_B, (size_t)ldb_d * sb, B, (size_t)ldb * sb, (size_t)n * sb, (size_t)k,
-                                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        st = spmm_csr_ex(m, k, n, nnz, d_rp, d_col, d_val, vals_type, d_B, b_type, ldb_d, d_C, c_type, ldc_d, alg,
-                         tuning, nullptr, 0, nullptr, stream);
-    else
-        st = cuda_status(e);
-    if (st == SPMM_OK) {
-        e = ldc == ldc_d ? cudaMemcpyAsync(C, d_C, (size_t)m * ldc_d * sc, cudaMemcpyDeviceToHost, s)
-                         : cudaMemcpy2DAsync(C, (size_t)ldc * sc, d_C, (size_t)ldc_d * sc, (size_t)n * sc, (size_t)m,
-                                             cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) st = cuda_status(e);
+    unsigned char* d_B = base + b_rp + b_col + b_val;
+    unsigned char* d_C = base + b_rp + b_col + b_val + b_B;
+    std::vector<cudaEvent_t> ev(2 + 2 * (size_t)slabs, nullptr);
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    cudaEvent_t e_alloc = ev[0], e_a = ev[1];
+    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_alloc, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, row_ptr, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col_ind, (size_t)nnz * 4, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, vals, (size_t)nnz * sv, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(e_a, up);
+    for (int j = 0; j < slabs && e == cudaSuccess; ++j) {
+        const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
+        if (k > 0 && nnz > 0)
+            e = (slabs == 1 && ldb == ldb_d)
+                    ? cudaMemcpyAsync(d_B, B, (size_t)k * ldb_d * sb, cudaMemcpyHostToDevice, up)
+                    : cudaMemcpy2DAsync(d_B + c0 * sb, (size_t)ldb_d * sb, static_cast<const unsigned char*>(B) + c0 * sb,
+                                        (size_t)ldb * sb, (size_t)cw * sb, (size_t)k, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + j], up);
     }
+    if (e != cudaSuccess) st = cuda_status(e);
+    // the selector's inputs are computed once for all slabs
+    spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
+    if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(s, e_a, 0));
+    if (st == SPMM_OK && alg == SPMM_ALG_AUTO_GB300 && t.max_row_len <= 0)
+        st = spmm_csr_max_row_length(m, d_rp, &t.max_row_len, stream);
+    for (int j = 0; j < slabs && st == SPMM_OK; ++j) {
+        const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
+        st = cuda_status(cudaStreamWaitEvent(s, ev[2 + j], 0));
+        if (st == SPMM_OK)
+            st = spmm_csr_ex(m, k, (int)cw, nnz, d_rp, d_col, d_val, vals_type, d_B + c0 * sb, b_type, ldb_d,
+                             d_C + c0 * sc, c_type, ldc_d, alg, &t, nullptr, 0, nullptr, stream);
+        if (st == SPMM_OK) st = cuda_status(cudaEventRecord(ev[2 + slabs + j], s));
+        if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, ev[2 + slabs + j], 0));
+        if (st == SPMM_OK)
+            st = cuda_status((slabs == 1 && ldc == ldc_d)
+                                 ? cudaMemcpyAsync(C, d_C, (size_t)m * ldc_d * sc, cudaMemcpyDeviceToHost, down)
+                                 : cudaMemcpy2DAsync(static_cast<unsigned char*>(C) + c0 * sc, (size_t)ldc * sc,
+                                                     d_C + c0 * sc, (size_t)ldc_d * sc, (size_t)cw * sc, (size_t)m,
+                                                     cudaMemcpyDeviceToHost, down));
+    }
+    // release after every stream that touched the buffer is done with it
+    cudaStreamSynchronize(up);
+    cudaStreamSynchronize(down);
     e = cudaFreeAsync(mem, s);
     if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
     e = cudaStreamSynchronize(s);
     if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
     return st;
 }
 

@@ -181,16 +181,38 @@ def test_bounded_wait_reports_timeout_and_context_survives(gpu_lib):
     check(run(pkg, torch, rp, ci, v, B, "merge").cpu().numpy(), rp, ci, v, B)
 
 
-def test_host_buffers_entry_point(gpu_lib):
+@pytest.mark.parametrize("n", [8, 13, 64, 128, 300])
+def test_host_buffers_entry_point(gpu_lib, n):
+    """spmm_csr_host: host arrays in and out, B and C pipelined in column slabs
+    over the copy streams (one slab for narrow rows, up to four for wide ones)."""
     import torch
 
     pkg = gpu_lib
     rp, ci, v, k = structure("power_law")
-    B = gen.normal_matrix(k, 64, 4)
+    B = gen.normal_matrix(k, n, 4)
     for alg in ALGS:
-        C = torch.empty((len(rp) - 1, 64), dtype=torch.float32).pin_memory()
+        C = torch.empty((len(rp) - 1, n), dtype=torch.float32).pin_memory()
         pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), torch.from_numpy(B), C, alg=alg)
         check(C.numpy(), rp, ci, v, B)
+
+
+def test_host_buffers_strided_and_16bit(gpu_lib):
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("short_rows")
+    n = 96
+    Bbig = torch.from_numpy(gen.normal_matrix(k, n + 5, 6))
+    Cbig = torch.full((len(rp) - 1, n + 7), 3.0)
+    pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), Bbig[:, 2:2 + n],
+                  Cbig[:, 1:1 + n], alg="merge")
+    check(Cbig[:, 1:1 + n].numpy(), rp, ci, v, np.ascontiguousarray(Bbig[:, 2:2 + n].numpy()))
+    assert torch.all(Cbig[:, 0] == 3.0) and torch.all(Cbig[:, 1 + n:] == 3.0)
+    vb, Bb = torch.from_numpy(v).to(torch.bfloat16), torch.from_numpy(gen.normal_matrix(k, 128, 7)).to(torch.bfloat16)
+    Cb = torch.empty((len(rp) - 1, 128), dtype=torch.float32)
+    pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), vb, Bb, Cb, alg="auto_gb300")
+    D = oracle.abs_bound(rp, ci, vb.double().numpy(), Bb.double().numpy())
+    assert oracle.normalized_error(Cb.numpy(), oracle.spmm(rp, ci, vb.double().numpy(), Bb.double().numpy()), D) <= FP32_TOL
 
 
 def test_plain_fp32_workload_full(gpu_lib):
