@@ -58,6 +58,26 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(value: float) -> float:
+    """The largest value over all ranks of the process group (the value itself
+    when no group of size > 1 is initialised).  Replicas are timed separately and
+    the job takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each did flops_per_rank in ms."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -314,14 +334,9 @@ def main():
     launches = pkg.spmm_launch_count() - launches0
     step_ms = [sum(per_call[n][s] for n in ns) for s in range(args.steps)]
     local_ms = float(statistics.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([local_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    else:
-        ms = local_ms
+    ms = max_over_ranks(local_ms)
     flops_step = sum(2.0 * nnz * n for n in ns)
-    value = world * flops_step / (ms * 1e-3) / 1e9
+    value = whole_job_gflops(flops_step, world, ms)
 
     peak, peak_src = peaks()
     # dominant kernel: the (alg, n) call with the largest share of the step; roofline of its family
