@@ -13,7 +13,12 @@
 namespace spmm {
 
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kThreads = 256;  // threads per CTA of every SpMM kernel
+constexpr int kThreads = 256;       // threads per CTA of the row-split, SDDMM and batched kernels
+// CTA shape of the merge-based kernel for W lanes per row: narrow rows (W <= 8)
+// use 128-thread CTAs with 1024-item tiles (small barrier domains, six CTAs per
+// SM); wide rows use 256-thread CTAs with 2048-item tiles (fewer tiles).
+__host__ __device__ constexpr int merge_cta_threads(int W) { return W >= 16 ? 256 : 128; }
+__host__ __device__ constexpr int merge_tile_items(int W) { return W >= 16 ? 2048 : 1024; }
 constexpr int kUnroll = 8;     // gathers of B in flight per lane
 
 // ------------------------------------------------------------------ element types
@@ -148,6 +153,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor drains; pdl_wait() returns once
+// the predecessor grid has completed and its memory is visible (a no-op when
+// the kernel was launched without the attribute).  pdl_launch_dependents()
+// lets the next kernel in the stream be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void report(int* status, int code) {
     if (status) atomicCAS(status, 0, code);

@@ -143,9 +143,9 @@ struct MergeArgs {
 // Shared-memory plan of the merge kernel: two staging buffers (row_ptr window,
 // col_ind window, vals window), then the per-lane-group first-row and carry
 // partial sums used to combine rows that cross lane groups inside a tile.
-template <typename TV, int VEC, int W>
+template <typename TV, int VEC, int W, int NT = kThreads>
 struct MergeSmem {
-    static constexpr int S = kThreads / W;  // lane groups per CTA
+    static constexpr int S = NT / W;  // lane groups per CTA of NT threads
     static constexpr int SW = W * VEC;      // columns per slab
     static __host__ __device__ int ipt(int ips) { return S * ips; }
     static __host__ __device__ int rp_cap(int ips) { return ipt(ips) + 8; }
@@ -181,9 +181,9 @@ __device__ __forceinline__ Window make_window(long long lo, long long hi, long l
     return w;
 }
 
-template <typename TV, int VEC, int W>
+template <typename TV, int VEC, int W, int NT = kThreads>
 struct MergeView {
-    using L = MergeSmem<TV, VEC, W>;
+    using L = MergeSmem<TV, VEC, W, NT>;
     unsigned char* base;
     int ips;
     __device__ uint64_t* bar(int b) const { return reinterpret_cast<uint64_t*>(base) + b; }
@@ -212,8 +212,8 @@ struct MergeView {
 // With TMA, lane 0 announces the byte count on the buffer's mbarrier and
 // issues up to three 1-D bulk copies; the array tails (at most 15 bytes each)
 // are loaded by the other lanes.  Without TMA the caller loads cooperatively.
-template <typename TV, int VEC, int W>
-__device__ __forceinline__ void merge_stage(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
+template <typename TV, int VEC, int W, int NT>
+__device__ __forceinline__ void merge_stage(const MergeArgs& a, const MergeView<TV, VEC, W, NT>& v, int item, int b) {
     const int lane = threadIdx.x & 31;
     const int tile = item % a.num_tiles;
     int2 l0 = make_int2(0, 0), l1 = make_int2(0, 0);
@@ -260,8 +260,9 @@ __device__ __forceinline__ void merge_stage(const MergeArgs& a, const MergeView<
 
 // Cooperative (all threads) load of a tile's windows, used when an array
 // base is not 16-byte aligned.  Uses the same smem indexing as merge_stage.
-template <typename TV, int VEC, int W>
-__device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
+template <typename TV, int VEC, int W, int NT>
+__device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const MergeView<TV, VEC, W, NT>& v, int item,
+                                                 int b) {
     const int tile = item % a.num_tiles;
     const int2 l0 = a.limits[tile], l1 = a.limits[tile + 1];
     const int r0 = l0.x, z0 = l0.y, r1 = l1.x, z1 = l1.y;
@@ -290,9 +291,9 @@ __device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const Merge
 // barrier.  Of the tile as a whole, the partial sum of a row that began in an
 // earlier tile (head) and of the row left unfinished at its end (carry) go to
 // global memory for the fix-up pass.
-template <typename TV, typename TB, typename TC, int VEC, int W>
-__device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<TV, VEC, W>& v, int item, int b) {
-    using L = MergeSmem<TV, VEC, W>;
+template <typename TV, typename TB, typename TC, int VEC, int W, int NT>
+__device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<TV, VEC, W, NT>& v, int item, int b) {
+    using L = MergeSmem<TV, VEC, W, NT>;
     constexpr int U = kUnroll;
     constexpr int CV = (U > W) ? U / W : 1;
     constexpr int BS = W * CV;
@@ -456,18 +457,21 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
 // records SPMM_ERR_TIMEOUT, waits (bounded) for its copies still in flight
 // and returns.
 template <typename TV, typename TB, typename TC, int VEC, int W>
-__global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
+__device__ __forceinline__ void merge_kernel_body(const MergeArgs& a) {
+    constexpr int NT = merge_cta_threads(W);
     extern __shared__ __align__(128) unsigned char smem[];
-    MergeView<TV, VEC, W> v{smem, a.ips};
+    MergeView<TV, VEC, W, NT> v{smem, a.ips};
+    pdl_wait();               // the partition (launched just before) has finished writing limits
+    pdl_launch_dependents();  // the fix-up may be scheduled; it waits for this grid to finish
     const int total = a.num_tiles * a.slabs;
     int item = blockIdx.x;
     if (item >= total) return;
     const int warp = threadIdx.x >> 5;
     if (!a.use_tma) {
         for (; item < total; item += gridDim.x) {
-            merge_load_plain<TV, VEC, W>(a, v, item, 0);
+            merge_load_plain<TV, VEC, W, NT>(a, v, item, 0);
             __syncthreads();
-            merge_tile<TV, TB, TC, VEC, W>(a, v, item, 0);
+            merge_tile<TV, TB, TC, VEC, W, NT>(a, v, item, 0);
             __syncthreads();
         }
         return;
@@ -480,13 +484,13 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
     __syncthreads();
     uint32_t phase = 0u;   // bit b: parity of the next phase of buffer b's mbarrier
     uint32_t pending = 0u; // bit b: a copy into buffer b is in flight
-    if (warp == 0) merge_stage<TV, VEC, W>(a, v, item, 0);
+    if (warp == 0) merge_stage<TV, VEC, W, NT>(a, v, item, 0);
     pending |= 1u;
     for (int it = 0; item < total; ++it, item += gridDim.x) {
         const int b = it & 1;
         const int nxt = item + gridDim.x;
         if (nxt < total) {
-            if (warp == 0) merge_stage<TV, VEC, W>(a, v, nxt, b ^ 1);
+            if (warp == 0) merge_stage<TV, VEC, W, NT>(a, v, nxt, b ^ 1);
             pending |= 2u >> b;  // bit (b ^ 1)
         }
         const uint32_t par = (phase >> b) & 1u;
@@ -500,34 +504,50 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
         }
         phase ^= 1u << b;
         pending &= ~(1u << b);
-        merge_tile<TV, TB, TC, VEC, W>(a, v, item, b);
+        merge_tile<TV, TB, TC, VEC, W, NT>(a, v, item, b);
         __syncthreads();
     }
+}
+
+// Narrow rows (W <= 8): 128-thread CTAs, six per SM.
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__global__ void __launch_bounds__(128, 6) merge_kernel_narrow(MergeArgs a) {
+    merge_kernel_body<TV, TB, TC, VEC, W>(a);
+}
+
+// Wide rows (W >= 16): 256-thread CTAs.
+template <typename TV, typename TB, typename TC, int VEC, int W>
+__global__ void __launch_bounds__(256) merge_kernel_wide(MergeArgs a) {
+    merge_kernel_body<TV, TB, TC, VEC, W>(a);
 }
 
 // FIXCARRYOUT of Algorithm 1.  For every run of consecutive tiles whose
 // carry-out belongs to the same row R (a row spanning several tiles), the row
 // is finished by the tile right after the run, which left R's remaining
 // partial sum in head[]; C[R] = carries (in tile order) + head, rounded once.
-// One CTA per tile; only run heads do work.
+// One warp per tile (grid-stride); only run heads do work, lanes stride n.
 template <typename TC>
 __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int* __restrict__ head_row,
                                    const float* __restrict__ carry, const float* __restrict__ head, int num_tiles,
                                    int n, TC* __restrict__ C, long long ldc, int* status) {
-    const int i = blockIdx.x;
-    const int R = carry_row[i];
-    if (R < 0 || (i > 0 && carry_row[i - 1] == R)) return;
-    int j = i;
-    while (j + 1 < num_tiles && carry_row[j + 1] == R) ++j;
-    if (j + 1 >= num_tiles || head_row[j + 1] != R) {
-        if (threadIdx.x == 0) report(status, SPMM_ERR_BAD_CSR);
-        return;
-    }
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        float sum = 0.0f;
-        for (int t = i; t <= j; ++t) sum += carry[(size_t)t * n + c];
-        sum += head[(size_t)(j + 1) * n + c];
-        C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
+    pdl_wait();  // launched early behind the merge kernel: its writes are visible after this
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < num_tiles; i += warps) {
+        const int R = carry_row[i];
+        if (R < 0 || (i > 0 && carry_row[i - 1] == R)) continue;
+        int j = i;
+        while (j + 1 < num_tiles && carry_row[j + 1] == R) ++j;
+        if (j + 1 >= num_tiles || head_row[j + 1] != R) {
+            if (lane == 0) report(status, SPMM_ERR_BAD_CSR);
+            continue;
+        }
+        for (int c = lane; c < n; c += 32) {
+            float sum = 0.0f;
+            for (int t = i; t <= j; ++t) sum += carry[(size_t)t * n + c];
+            sum += head[(size_t)(j + 1) * n + c];
+            C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
+        }
     }
 }
 

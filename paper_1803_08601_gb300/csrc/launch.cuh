@@ -74,8 +74,13 @@ cudaError_t rowsplit_launch(const RowSplitArgs& a, const Shape& s, cudaStream_t 
 
 template <typename TV, typename TB, typename TC, int VEC, int W>
 cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
-    using L = MergeSmem<TV, VEC, W>;
-    auto kern = merge_kernel<TV, TB, TC, VEC, W>;
+    constexpr int NT = merge_cta_threads(W);
+    using L = MergeSmem<TV, VEC, W, NT>;
+    auto kern = [] {
+        if constexpr (NT == 256) return merge_kernel_wide<TV, TB, TC, VEC, W>;
+        else return merge_kernel_narrow<TV, TB, TC, VEC, W>;
+    }();
+    static_assert(NT == 128 || NT == 256, "merge CTA shapes");
     const size_t smem = L::total(s.ips);
     // per-instantiation cache of the opt-in shared-memory size and occupancy
     static thread_local int cached_dev = -1;
@@ -88,7 +93,7 @@ cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, c
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int blocks = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, NT, smem);
         if (e != cudaSuccess) return e;
         cached_dev = dev;
         cached_smem = smem;
@@ -98,8 +103,18 @@ cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, c
     long long grid = (long long)cached_blocks * grid_cap;
     if (grid > items) grid = items;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, kThreads, smem, st>>>(a);
-    e = cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // overlap the partition's tail
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
     return e;
 }
@@ -127,12 +142,12 @@ cudaError_t merge_launch(const MergeArgs& a, const Shape& s, int grid_cap, cudaS
 template <typename TV, int VEC>
 size_t merge_smem_vec(const Shape& s) {
     switch (s.W) {
-        case 1: return MergeSmem<TV, VEC, 1>::total(s.ips);
-        case 2: return MergeSmem<TV, VEC, 2>::total(s.ips);
-        case 4: return MergeSmem<TV, VEC, 4>::total(s.ips);
-        case 8: return MergeSmem<TV, VEC, 8>::total(s.ips);
-        case 16: return MergeSmem<TV, VEC, 16>::total(s.ips);
-        default: return MergeSmem<TV, VEC, 32>::total(s.ips);
+        case 1: return MergeSmem<TV, VEC, 1, merge_cta_threads(1)>::total(s.ips);
+        case 2: return MergeSmem<TV, VEC, 2, merge_cta_threads(2)>::total(s.ips);
+        case 4: return MergeSmem<TV, VEC, 4, merge_cta_threads(4)>::total(s.ips);
+        case 8: return MergeSmem<TV, VEC, 8, merge_cta_threads(8)>::total(s.ips);
+        case 16: return MergeSmem<TV, VEC, 16, merge_cta_threads(16)>::total(s.ips);
+        default: return MergeSmem<TV, VEC, 32, merge_cta_threads(32)>::total(s.ips);
     }
 }
 

@@ -20,21 +20,38 @@ std::atomic<long long> g_launches{0};
 //
 // Phase 1 (PARTITIONSPMM): one thread per tile boundary finds the boundary's
 // (rows, nonzeros) coordinate by binary search on its diagonal.
+// One warp per tile boundary: a 32-ary search on the boundary's diagonal.  The
+// predicate "row x ends no later than nonzero d-x-1" (row_ptr[x+1] <= d-x-1)
+// holds exactly for x below the number of row ends among the first d merged
+// items; every round the 32 lanes test 32 evenly spaced candidates and the
+// ballot narrows the interval about 32-fold, so a diagonal of 10^7 items
+// needs about 6 rounds of dependent loads instead of 24.
 __global__ void merge_partition_kernel(const int* __restrict__ row_ptr, int m, long long nnz, int items_per_tile,
                                        int num_tiles, int2* __restrict__ limits) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > num_tiles) return;
+    pdl_launch_dependents();  // the merge kernel may be scheduled now; it waits for this grid to finish
+    const int lane = threadIdx.x & 31;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t > num_tiles) return;  // whole warps exit together
     const long long total = (long long)m + nnz;
-    long long d = (long long)t * items_per_tile;
+    long long d = t * items_per_tile;
     if (d > total) d = total;
-    long long lo = d - nnz > 0 ? d - nnz : 0;
+    long long lo = d - nnz > 0 ? d - nnz : 0;  // answer in [lo, hi]
     long long hi = d < m ? d : m;
-    while (lo < hi) {  // number of row ends among the first d merged items
-        const long long mid = (lo + hi) >> 1;
-        if ((long long)__ldg(row_ptr + mid + 1) <= d - mid - 1) lo = mid + 1;
-        else hi = mid;
+    while (hi > lo) {
+        const long long span = hi - lo;
+        const long long x = lo + (span * lane) / 32;  // candidates lo .. hi-1, increasing with the lane
+        const bool p = (long long)__ldg(row_ptr + x + 1) <= d - x - 1;
+        const unsigned ball = __ballot_sync(kFullMask, p);
+        const int cnt = __popc(ball);  // the predicate holds on a prefix of the lanes
+        if (cnt == 0) {
+            hi = lo;
+        } else {
+            const long long x_last = lo + (span * (cnt - 1)) / 32;
+            if (cnt < 32) hi = lo + (span * cnt) / 32;
+            lo = x_last + 1;
+        }
     }
-    limits[t] = make_int2((int)lo, (int)(d - lo));
+    if (lane == 0) limits[t] = make_int2((int)lo, (int)(d - lo));
 }
 
 // Bounded-wait self test: waits on a phase that nothing completes.
@@ -126,8 +143,8 @@ bool shape_for(int n, int vec, const spmm_tuning_t* t, Shape* s) {
     s->W = W;
     s->slabs = (int)((chunks + W - 1) / W);
     if (s->slabs > 65535) return false;
-    const int groups = kThreads / W;
-    int ips = (t && t->items_per_subwarp > 0) ? t->items_per_subwarp : 2048 / groups;
+    const int groups = merge_cta_threads(W) / W;  // lane groups per merge CTA
+    int ips = (t && t->items_per_subwarp > 0) ? t->items_per_subwarp : merge_tile_items(W) / groups;
     if (ips < 4) ips = 4;
     if (ips > 4096) ips = 4096;
     s->ips = ips;
@@ -152,7 +169,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
     MergeLayout L{};
-    const long long ipt = (long long)(kThreads / s.W) * s.ips;
+    const long long ipt = (long long)(merge_cta_threads(s.W) / s.W) * s.ips;
     const long long total = (long long)m + nnz;
     L.num_tiles = (int)((total + ipt - 1) / ipt);
     size_t off = 0;
@@ -344,10 +361,10 @@ int spmm_merge_partition(int m, long long nnz, const int* row_ptr, int items_per
     if (m < 0 || nnz < 0 || items_per_tile <= 0 || num_tiles < 0 || !limits || (m > 0 && !row_ptr))
         return SPMM_ERR_INVALID_VALUE;
     if ((long long)num_tiles * items_per_tile < (long long)m + nnz) return SPMM_ERR_INVALID_VALUE;
-    const int threads = 256;
-    const int blocks = (num_tiles + 1 + threads - 1) / threads;
-    merge_partition_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(row_ptr, m, nnz, items_per_tile, num_tiles,
-                                                                         reinterpret_cast<int2*>(limits));
+    const int threads = 256;  // 8 boundaries per block, one warp each
+    const long long blocks = ((long long)num_tiles + 1 + 7) / 8;
+    merge_partition_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
+        row_ptr, m, nnz, items_per_tile, num_tiles, reinterpret_cast<int2*>(limits));
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
     return cuda_status(e);
@@ -423,15 +440,25 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
     ma.use_tma = ((uintptr_t)row_ptr % 16 == 0) && ((uintptr_t)col_ind % 16 == 0) && ((uintptr_t)vals % 16 == 0);
     ma.wait_ns = kWaitLimitNs;
 
-    const int ipt = (kThreads / shape.W) * shape.ips;
+    const int ipt = (merge_cta_threads(shape.W) / shape.W) * shape.ips;
     st = spmm_merge_partition(m, nnz, row_ptr, ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
                               stream);
     if (st == SPMM_OK) st = cuda_status(L->merge(ma, shape, sm_count(), s));
     if (st == SPMM_OK && lay.num_tiles > 1) {
         auto fix = [&](auto* c) {
             using TC = std::remove_pointer_t<decltype(c)>;
-            merge_fixup_kernel<TC><<<lay.num_tiles, 128, 0, s>>>(ma.carry_row, ma.head_row, ma.carry, ma.head,
-                                                                 lay.num_tiles, n, static_cast<TC*>(C), ldc, d_status);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)std::min<long long>(((long long)lay.num_tiles + 7) / 8, 152LL * 8));
+            cfg.blockDim = dim3(256);
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, merge_fixup_kernel<TC>, (const int*)ma.carry_row, (const int*)ma.head_row,
+                               (const float*)ma.carry, (const float*)ma.head, lay.num_tiles, n, static_cast<TC*>(C),
+                               ldc, d_status);
         };
         if (c_type == SPMM_F32) fix(static_cast<float*>(nullptr));
         else if (c_type == SPMM_BF16) fix(static_cast<__nv_bfloat16*>(nullptr));
