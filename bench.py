@@ -50,11 +50,13 @@ def parse():
     p.add_argument("--workload", default="power_law", choices=["power_law", "plain"])
     p.add_argument("--n", type=int, nargs="*", default=None, help="dense widths (default 8 32 64 128)")
     p.add_argument("--alg", default="auto_gb300", choices=["auto_gb300", "auto", "row_split", "merge"])
-    p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown "
+                   "(the growth forms are controlled by --forms)")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--tuning", default=None, help='JSON spmm_tuning_t fields, e.g. {"column_slabs": 2}')
     p.add_argument("--forms", default="precision,backward,batched",
                    help="comma list of growth forms measured after the headline (empty: none)")
+    p.add_argument("--batched-count", type=int, default=2048, help="matrices in the batched form")
     return p.parse_args()
 
 
@@ -377,11 +379,13 @@ def main():
             line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
                                     "sample": f"{passes} pass(es) over {nrows} seeded random rows of the {label} "
                                               f"matrix, all n, {t:.1f} s"}
+    forms = [f for f in args.forms.split(",") if f]
+    if rank == 0 and forms:
         del d_B, d_C, ws
         torch.cuda.empty_cache()
         line["forms"] = {}
-        for form in [f for f in args.forms.split(",") if f]:
-            line["forms"][form] = FORMS[form](pkg, torch, flush, stream, args.steps)
+        for form in forms:
+            line["forms"][form] = FORMS[form](pkg, torch, flush, stream, args.steps, args)
             torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -463,7 +467,7 @@ def _norm_diff(torch, C, C_ref, D):
     return float("inf") if bad_zero else float((diff[nz] / D[nz]).max().item())
 
 
-def form_precision(pkg, torch, flush, stream, steps):
+def form_precision(pkg, torch, flush, stream, steps, args):
     """2M x 2M, 32 nonzeros per row, n = 128: 16-bit storage vs the float32 plain kernel."""
     a, Bf = gen.workload_precision()
     dev = torch.device("cuda")
@@ -494,7 +498,7 @@ def form_precision(pkg, torch, flush, stream, steps):
     return out
 
 
-def form_backward(pkg, torch, flush, stream, steps):
+def form_backward(pkg, torch, flush, stream, steps, args):
     """GCN layer (500k nodes, mean degree ~20, n = 256): forward, dX = A^T dY, dvals = SDDMM."""
     a, X = gen.workload_gcn()
     dev = torch.device("cuda")
@@ -531,9 +535,9 @@ def form_backward(pkg, torch, flush, stream, steps):
             "speedup_fwd_vs_f32_plain": t_plain / t_fwd}
 
 
-def form_batched(pkg, torch, flush, stream, steps):
+def form_batched(pkg, torch, flush, stream, steps, args):
     """2048 CSR matrices of uneven sizes in one persistent graph-captured launch vs a loop of launches."""
-    s = gen.workload_batched()
+    s = gen.workload_batched(count=args.batched_count)
     dev = torch.device("cuda")
     rps, cis, vs, Bs, Cs = [], [], [], [], []
     g = torch.Generator(device=dev).manual_seed(gen.SEED_BASE + 5)
@@ -544,7 +548,8 @@ def form_batched(pkg, torch, flush, stream, steps):
         Bs.append(torch.randn(a.k, n, device=dev, generator=g))
         Cs.append(torch.empty((a.m, n), device=dev))
     flops = sum(2.0 * a.nnz * n for a, n in zip(s.mats, s.ns))
-    out = {"workload": "2048 matrices, m log-uniform [64, 65536], Poisson rows lambda U[4,64], n in {32,64,128}",
+    out = {"workload": f"{args.batched_count} matrices, m log-uniform [64, 65536], Poisson rows lambda U[4,64], "
+                       "n in {32,64,128}",
            "total_nnz": s.info["total_nnz"], "total_rows": s.info["total_rows"]}
     for pol_name, pol in (("model", pkg.BATCHED_MODEL), ("autotune", pkg.BATCHED_AUTOTUNE)):
         torch.cuda.synchronize()
