@@ -68,29 +68,35 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_SIGS = {
+    "oracle_spmm_f64": "i64 i64 vp vp vp vp i64 vp i64",
+    "oracle_spmm_rows_f64": "i64 vp i64 vp vp vp vp i64 vp",
+    "oracle_absbound_rows_f64": "i64 vp i64 vp vp vp vp i64 vp",
+    "oracle_spmm_t_f64": "i64 i64 i64 vp vp vp vp i64 vp i64",
+    "oracle_sddmm_f64": "i64 i64 vp vp vp i64 vp i64 vp",
+    "oracle_sddmm_absbound_f64": "i64 i64 vp vp vp i64 vp i64 vp",
+    "oracle_csr_transpose": "i64 i64 vp vp vp vp vp",
+    "oracle_merge_path_limits": "i64 vp i64 i64 vp",
+    "oracle_set_num_threads": "int",
+    "oracle_num_threads": "",
+}
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    kinds = {"i64": ctypes.c_int64, "vp": ctypes.c_void_p, "int": ctypes.c_int}
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = [kinds[a] for a in args.split()]
+        fn.restype = ctypes.c_int if name == "oracle_num_threads" else None
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i64, vp = ctypes.c_int64, ctypes.c_void_p
-            sig = {
-                "oracle_spmm_f64": [i64, i64, vp, vp, vp, vp, i64, vp, i64],
-                "oracle_spmm_rows_f64": [i64, vp, i64, vp, vp, vp, vp, i64, vp],
-                "oracle_absbound_rows_f64": [i64, vp, i64, vp, vp, vp, vp, i64, vp],
-                "oracle_spmm_t_f64": [i64, i64, i64, vp, vp, vp, vp, i64, vp, i64],
-                "oracle_sddmm_f64": [i64, i64, vp, vp, vp, i64, vp, i64, vp],
-                "oracle_sddmm_absbound_f64": [i64, i64, vp, vp, vp, i64, vp, i64, vp],
-                "oracle_csr_transpose": [i64, i64, vp, vp, vp, vp, vp],
-                "oracle_merge_path_limits": [i64, vp, i64, i64, vp],
-                "oracle_set_num_threads": [ctypes.c_int],
-                "oracle_num_threads": [],
-            }
-            for name, args in sig.items():
-                fn = getattr(lib, name)
-                fn.argtypes = args
-                fn.restype = ctypes.c_int if name == "oracle_num_threads" else None
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 
