@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--forms", default="precision,backward,batched",
                    help="comma list of growth forms measured after the headline (empty: none)")
     p.add_argument("--batched-count", type=int, default=2048, help="matrices in the batched form")
+    p.add_argument("--sweep", default=None, choices=["aspect", "density"],
+                   help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
+                        "n = 64) or the density sweep against dense GEMM (100k x 100k, n = 64); JSON line per point")
     return p.parse_args()
 
 
@@ -267,6 +270,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     import torch
 
     import paper_1803_08601_gb300 as pkg
@@ -571,6 +576,74 @@ def form_batched(pkg, torch, flush, stream, steps, args):
 
 
 FORMS = {"precision": form_precision, "backward": form_backward, "batched": form_batched}
+
+
+# ----------------------------------------------------------------------------- sweeps
+
+def run_sweep(args):
+    """Parameter sweeps of the two families (one JSON line per point; not the benchmark)."""
+    import torch
+
+    import paper_1803_08601_gb300 as pkg
+
+    pkg.build()
+    pkg.load()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4 + 1024, device=dev)
+    reps = max(3, min(args.steps, 5))
+    n = 64
+    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    if args.sweep == "aspect":
+        # dense matrices stored as CSR, from 2 rows of 2^23 nonzeros to 2^23 rows of 2 (the paper's Fig. 1 / Fig. 4)
+        total = 1 << 24
+        for lg in range(1, 24):
+            m, k = 1 << lg, total >> lg
+            rp = torch.arange(0, total + 1, k, dtype=torch.int32, device=dev)
+            ci = torch.arange(k, dtype=torch.int32, device=dev).repeat(m)
+            v = torch.rand(total, device=dev, generator=torch.Generator(device=dev).manual_seed(lg)) * 2 - 1
+            B = torch.randn(k, n, device=dev, generator=torch.Generator(device=dev).manual_seed(100 + lg))
+            C = torch.empty(m, n, device=dev)
+            ws = torch.empty(pkg.workspace_size(m, k, n, total, "merge"), dtype=torch.uint8, device=dev)
+            row = {"sweep": "aspect", "m": m, "k": k, "nnz": total, "n": n,
+                   "paper_pick": name[pkg.spmm_select_alg(m, total, 0.0)],
+                   "gb300_pick": name[pkg.spmm_select_alg_gb300(m, total, k, n, pkg.F32)]}
+            for alg in ("row_split", "merge"):
+                r = reps if (alg == "merge" or k <= (1 << 16)) else 1  # very long rows: one timed run
+                t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=total, workspace=ws),
+                          flush, stream, r)
+                row[alg] = {"ms": t, "gflops": 2.0 * total * n / t / 1e6}
+            print(json.dumps(row), flush=True)
+            del rp, ci, v, B, C, ws
+            torch.cuda.empty_cache()
+    else:
+        # fixed fraction of nonzeros per row of a 100k x 100k matrix vs dense GEMM (the paper's Fig. 7)
+        mk = 100_000
+        B = torch.randn(mk, n, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        for frac in (0.0001, 0.001, 0.005, 0.01, 0.02, 0.05, 0.1):
+            per_row = max(1, int(round(frac * mk)))
+            a = gen.uniform_rows(mk, mk, per_row, gen.SEED_BASE + 70)
+            rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
+            del a
+            C = torch.empty(mk, n, device=dev)
+            lmax = per_row
+            tun = {"max_row_len": lmax}
+            row = {"sweep": "density", "m": mk, "k": mk, "per_row": per_row, "density": per_row / mk,
+                   "nnz": per_row * mk, "n": n, "gb300_pick": name[pkg.spmm_select_alg_gb300(mk, per_row * mk, lmax, n, pkg.F32)]}
+            t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg="auto_gb300", out=C, nnz=per_row * mk, tuning=tun),
+                      flush, stream, reps)
+            row["spmm"] = {"ms": t, "gflops": 2.0 * per_row * mk * n / t / 1e6}
+            dense = torch.zeros(mk, mk, device=dev)
+            dense.view(-1)[(torch.repeat_interleave(torch.arange(mk, device=dev), per_row) * mk + ci.long())] = v
+            for tf32 in (False, True):
+                torch.backends.cuda.matmul.allow_tf32 = tf32
+                t = _time(torch, lambda: torch.matmul(dense, B, out=C), flush, stream, reps)
+                row["gemm_tf32" if tf32 else "gemm_fp32"] = {"ms": t, "dense_tflops": 2.0 * mk * mk * n / t / 1e9}
+            torch.backends.cuda.matmul.allow_tf32 = False
+            print(json.dumps(row), flush=True)
+            del rp, ci, v, C, dense
+            torch.cuda.empty_cache()
+    return 0
 
 
 if __name__ == "__main__":

@@ -107,7 +107,8 @@ int spmm_select_alg(int m, long long nnz, double threshold);
  * SPMM_ALG_MERGE when either
  *   - the longest row is long enough to be the critical path of row split
  *     (Type 1 imbalance, Section 3.2): max_row_len > 1024 and
- *     max_row_len * 4096 > nnz, or
+ *     max_row_len * 8192 > nnz (fitted on a GB300 sweep of dense-as-CSR
+ *     matrices from 2 x 2^23 to 2^23 x 2), or
  *   - the mean row length nnz / m is below 5 and a row of B is at least 64
  *     bytes (n * element size of B); measured crossover of the two kernels on
  *     GB300 for uniform rows (the paper's 9.35 was measured on a K40c);

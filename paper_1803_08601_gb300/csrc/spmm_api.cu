@@ -307,7 +307,7 @@ int spmm_select_alg(int m, long long nnz, double threshold) {
 
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type) {
     if (m <= 0) return SPMM_ALG_ROW_SPLIT;
-    if (max_row_len > 1024 && max_row_len * 4096 > nnz) return SPMM_ALG_MERGE;  // Type 1 guard
+    if (max_row_len > 1024 && max_row_len * 8192 > nnz) return SPMM_ALG_MERGE;  // Type 1 guard
     const double d = (double)nnz / (double)m;
     const long long row_bytes = (long long)n * (dtype_size(b_type) ? dtype_size(b_type) : 4);
     if (row_bytes >= 64 && d < 5.0) return SPMM_ALG_MERGE;

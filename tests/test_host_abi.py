@@ -58,6 +58,9 @@ def test_gb300_selector(lib):
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 64, F) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 1_000, 64, F) == pkg.ALG_ROW_SPLIT
     assert pkg.spmm_select_alg_gb300(4096, 65_536, 16, 64, F) == pkg.ALG_ROW_SPLIT
+    # the aspect-ratio sweep's boundary: 4096 rows of 4096 go to merge, 8192 rows of 2048 to row split
+    assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 64, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(8192, 1 << 24, 2048, 64, F) == pkg.ALG_ROW_SPLIT
     # recalibrated mean-length rule: short rows go to merge only with rows of B of >= 64 bytes
     assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 64, F) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 8, F) == pkg.ALG_ROW_SPLIT
