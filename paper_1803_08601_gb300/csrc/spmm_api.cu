@@ -160,6 +160,22 @@ bool choose_shape(int n, int tb, int tc, const void* B, long long ldb, const voi
     return shape_for(n, vec_ok ? V : 1, t, s);
 }
 
+// Column slabs when B is much larger than L2 and its rows are wide: each pass
+// then gathers half of every row, over a B slab twice as likely to be found in
+// L2 (measured on GB300: merge with 512-byte rows and row split with >= 256-byte
+// rows of a B beyond L2 gain 6-14 %; narrower rows lose).
+int default_slabs(int alg, int k, int n, int b_type) {
+    static int l2_bytes[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (l2_bytes[dev] == 0 && cudaDeviceGetAttribute(&l2_bytes[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return 1;
+    const long long row_bytes = (long long)n * dtype_size(b_type);
+    if ((long long)k * row_bytes <= 2LL * l2_bytes[dev]) return 1;
+    const long long min_row = alg == SPMM_ALG_MERGE ? 512 : 256;
+    return row_bytes >= min_row ? 2 : 1;
+}
+
 struct MergeLayout {
     int num_tiles;
     size_t off_limits, off_carry_row, off_head_row, off_carry, off_head, total;
@@ -344,14 +360,20 @@ size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int 
     if (m < 0 || k < 0 || n < 0 || nnz < 0 || dtype_size(b_type) == 0) return 0;
     if (alg == SPMM_ALG_AUTO_GB300) alg = SPMM_ALG_MERGE;  // the choice may need the longest row: size for merge
     if (resolve_alg(alg, m, nnz, tuning) != SPMM_ALG_MERGE || m == 0 || n == 0) return 0;
-    // the access width depends on pointer alignment, unknown here: size for both widths
+    // the access width depends on pointer alignment and the default slab count on the device's L2,
+    // neither known here: size for every combination
     size_t best = 0;
     for (int vec : {1, 16 / dtype_size(b_type)}) {
-        Shape s;
-        if (!shape_for(n, vec, tuning, &s)) return 0;
-        clamp_tile(&s, 4);
-        const size_t need = merge_layout(m, nnz, n, s).total;
-        if (need > best) best = need;
+        for (int slabs : {0, 2}) {
+            spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
+            if (slabs && (t.column_slabs > 0 || t.lanes_per_row > 0)) continue;
+            if (slabs) t.column_slabs = slabs;
+            Shape s;
+            if (!shape_for(n, vec, &t, &s)) return 0;
+            clamp_tile(&s, 4);
+            const size_t need = merge_layout(m, nnz, n, s).total;
+            if (need > best) best = need;
+        }
     }
     return best;
 }
@@ -384,7 +406,6 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
         if (st != SPMM_OK) return st;
     }
     Shape shape;
-    if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, tuning, &shape)) return SPMM_ERR_INVALID_VALUE;
     if (alg == SPMM_ALG_AUTO_GB300) {
         long long lmax = tuning ? tuning->max_row_len : 0;
         if (lmax <= 0) {
@@ -394,6 +415,9 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
         alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
     }
     const int a = resolve_alg(alg, m, nnz, tuning);
+    spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
+    if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
+    if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
     if (a == SPMM_ALG_ROW_SPLIT) {
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
         return cuda_status(L->rowsplit(ra, shape, s));
