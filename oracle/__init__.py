@@ -23,6 +23,8 @@ What each function computes, and where the paper defines it:
 * ``spmm_t``                  dB = A^T dC by definition (no transpose formed).
 * ``sddmm``                   dvals[p] = <dC[i, :], B[col_ind[p], :]>.
 * ``csr_transpose``           stable counting-sort transpose with permutation.
+* ``spmm_semiring``           C = A (+).(x) B over (+,x), (min,+), (max,+), (max,x)
+  (the GraphBLAS matrix product of Section 1), by definition.
 
 The backward operations (``spmm_t``, ``sddmm``, ``csr_transpose``) are not in the
 paper, which names SpMM_T only as future work (Section 6); they are the standard
@@ -77,6 +79,7 @@ _SIGS = {
     "oracle_sddmm_absbound_f64": "i64 i64 vp vp vp i64 vp i64 vp",
     "oracle_csr_transpose": "i64 i64 vp vp vp vp vp",
     "oracle_merge_path_limits": "i64 vp i64 i64 vp",
+    "oracle_spmm_semiring_f64": "i64 i64 int vp vp vp vp i64 vp i64",
     "oracle_set_num_threads": "int",
     "oracle_num_threads": "",
 }
@@ -197,6 +200,22 @@ def normalized_error(C, C_ref, D, abs_floor: float = 0.0) -> float:
     return float((err[nz] / D[nz]).max()) if np.any(nz) else 0.0
 
 
+# ----------------------------------------------------------------------------- semirings
+
+SEMIRINGS = {"plus_times": 0, "min_plus": 1, "max_plus": 2, "max_times": 3}
+
+
+def spmm_semiring(row_ptr, col_ind, vals, B, semiring: str) -> np.ndarray:
+    """C = A (+).(x) B over the named semiring, in float64 (empty rows: the identity of (+))."""
+    rp, ci = _i32(row_ptr), _i32(col_ind)
+    v, b = to_f64(vals), to_f64(B)
+    m, n = rp.shape[0] - 1, b.shape[1]
+    c = np.empty((m, n), dtype=np.float64)
+    if m and n:
+        _load().oracle_spmm_semiring_f64(m, n, SEMIRINGS[semiring], _p(rp), _p(ci), _p(v), _p(b), b.shape[1], _p(c), n)
+    return c
+
+
 # ----------------------------------------------------------------------------- Section 5.4
 
 def select_alg(m: int, nnz: int, threshold: float = HEURISTIC_THRESHOLD) -> int:
@@ -270,5 +289,6 @@ def csr_transpose(row_ptr, col_ind, k: int):
 __all__ = [
     "HEURISTIC_THRESHOLD", "ALG_ROW_SPLIT", "ALG_MERGE", "build", "bf16_bits_to_f64", "to_f64",
     "set_threads", "num_threads", "spmm", "spmm_rows", "abs_bound_rows", "abs_bound", "normalized_error",
-    "select_alg", "merge_path_limits", "spmm_t", "sddmm", "sddmm_abs_bound", "csr_transpose",
+    "select_alg", "merge_path_limits", "spmm_t", "sddmm", "sddmm_abs_bound", "csr_transpose", "SEMIRINGS",
+    "spmm_semiring",
 ]

@@ -210,3 +210,30 @@ void oracle_merge_path_limits(int64_t m, const int32_t *row_ptr, int64_t items, 
         limits[2 * t + 1] = (int32_t)z;
     }
 }
+
+/*
+ * SpMM over a semiring (the GraphBLAS matrix-matrix product named in
+ * Section 1): C[i][j] = (+) over p in row i of (val[p] (x) B[col_ind[p]][j]),
+ * starting from the identity of (+); an empty row gives the identity.
+ * semiring 0: (+, x) with identity 0; 1: (min, +) with identity +inf;
+ * 2: (max, +) with identity -inf; 3: (max, x) with identity -inf.
+ */
+void oracle_spmm_semiring_f64(int64_t m, int64_t n, int semiring, const int32_t *row_ptr, const int32_t *col_ind,
+                              const double *val, const double *B, int64_t ldb, double *C, int64_t ldc) {
+    const double ident = semiring == 0 ? 0.0 : semiring == 1 ? INFINITY : -INFINITY;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i) {
+        double *c = C + i * ldc;
+        for (int64_t j = 0; j < n; ++j) c[j] = ident;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            const double a = val[p];
+            const double *b = B + (int64_t)col_ind[p] * ldb;
+            for (int64_t j = 0; j < n; ++j) {
+                if (semiring == 0) c[j] += a * b[j];
+                else if (semiring == 1) c[j] = fmin(c[j], a + b[j]);
+                else if (semiring == 2) c[j] = fmax(c[j], a + b[j]);
+                else c[j] = fmax(c[j], a * b[j]);
+            }
+        }
+    }
+}

@@ -39,6 +39,9 @@ MUTANTS = {
         "void oracle_csr_transpose(", "for (int64_t i = 0; i < m; ++i)", "for (int64_t i = m - 1; i >= 0; --i)"),
     "merge walk takes the nonzero first on ties": (
         "void oracle_merge_path_limits(", "row_ptr[r + 1] <= z", "row_ptr[r + 1] < z"),
+    "(min,+) starts from 0 instead of +inf": (
+        "void oracle_spmm_semiring_f64(", "semiring == 1 ? INFINITY", "semiring == 1 ? 0.0"),
+    "(max,x) multiplies into a sum": ("void oracle_spmm_semiring_f64(", "c[j] = fmax(c[j], a * b[j])", "c[j] += a * b[j]"),
 }
 
 
@@ -110,7 +113,21 @@ def check_merge_path(rng):
         assert (r == 0 or rp[r] <= z) and (r == m or z == 0 or rp[r + 1] >= z)
 
 
-CHECKS = [check_products, check_transpose, check_merge_path]
+def check_semirings(rng):
+    m, k, n = 13, 9, 4
+    rp, ci, v = _random_csr(rng, m, k, dup=False)
+    B = rng.standard_normal((k, n))
+    full = np.full((m, k), np.inf)
+    full[np.repeat(np.arange(m), np.diff(rp)), ci] = v
+    np.testing.assert_array_equal(oracle.spmm_semiring(rp, ci, v, B, "min_plus"),
+                                  np.min(full[:, :, None] + B[None], axis=1))
+    C = oracle.spmm_semiring(rp, ci, v, np.ones((k, n)), "max_times")
+    for i in range(m):
+        seg = v[rp[i]:rp[i + 1]]
+        assert np.all(C[i] == (seg.max() if seg.size else -np.inf))
+
+
+CHECKS = [check_products, check_transpose, check_merge_path, check_semirings]
 
 
 def test_real_oracle_passes_every_check():

@@ -337,3 +337,50 @@ def test_bf16_widening_matches_torch():
     # the bfloat16 rounding of float32 is to nearest, so the error is at most half a unit in the last place
     rel = np.abs(oracle.bf16_bits_to_f64(bits[:5000]) - x[:5000]) / np.abs(x[:5000])
     assert rel.max() <= 2.0 ** -8
+
+
+# ----------------------------------------------------------------------------- semirings
+
+def _masked(rp, ci, v, m, k, fill):
+    """Dense m x k copy of A with `fill` where nothing is stored (no duplicates)."""
+    d = np.full((m, k), fill)
+    d[np.repeat(np.arange(m), np.diff(rp)), ci] = v
+    return d
+
+
+def test_semiring_min_plus_against_numpy_broadcast():
+    rng = np.random.default_rng(31)
+    m, k, n = 17, 23, 9
+    rp, ci, v = random_csr(rng, m, k)
+    B = rng.standard_normal((k, n))
+    ref = np.min(_masked(rp, ci, v, m, k, np.inf)[:, :, None] + B[None, :, :], axis=1)
+    np.testing.assert_array_equal(oracle.spmm_semiring(rp, ci, v, B, "min_plus"), ref)
+    ref = np.max(_masked(rp, ci, v, m, k, -np.inf)[:, :, None] + B[None, :, :], axis=1)
+    np.testing.assert_array_equal(oracle.spmm_semiring(rp, ci, v, B, "max_plus"), ref)
+    np.testing.assert_allclose(oracle.spmm_semiring(rp, ci, v, B, "plus_times"), oracle.spmm(rp, ci, v, B), rtol=0,
+                               atol=0)
+
+
+def test_semiring_closed_forms():
+    rng = np.random.default_rng(32)
+    m, n = 40, 7
+    B = rng.standard_normal((m, n))
+    ident = np.arange(m + 1, dtype=np.int32)
+    # (min,+) with the (min,+) identity matrix (zeros on the diagonal): C = B
+    assert np.array_equal(oracle.spmm_semiring(ident, np.arange(m, dtype=np.int32), np.zeros(m), B, "min_plus"), B)
+    # (max,x) with B = ones: the row maxima of A; empty rows give -inf
+    rp, ci, v = random_csr(rng, m, 30, empty_every=4)
+    C = oracle.spmm_semiring(rp, ci, v, np.ones((30, n)), "max_times")
+    for i in range(m):
+        seg = v[rp[i]:rp[i + 1]]
+        assert np.all(C[i] == (seg.max() if seg.size else -np.inf))
+    # one relaxation step of shortest paths on a path graph 0 -> 1 -> 2 -> 3 (edge weight 1):
+    # D1 = A (min,+) D0 with D0 the distances from node 3 reached in at most 0 hops
+    rp = np.array([0, 1, 2, 3, 3], np.int32)
+    ci = np.array([1, 2, 3], np.int32)
+    w = np.ones(3)
+    D0 = np.array([[np.inf], [np.inf], [np.inf], [0.0]])
+    D1 = np.minimum(D0, oracle.spmm_semiring(rp, ci, w, D0, "min_plus"))
+    D2 = np.minimum(D1, oracle.spmm_semiring(rp, ci, w, D1, "min_plus"))
+    D3 = np.minimum(D2, oracle.spmm_semiring(rp, ci, w, D2, "min_plus"))
+    assert D3[:, 0].tolist() == [3.0, 2.0, 1.0, 0.0]
