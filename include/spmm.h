@@ -153,6 +153,31 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int *row_ptr, const in
                 int c_type, long long ldc, int alg, const spmm_tuning_t *tuning, void *workspace,
                 size_t workspace_bytes, int *d_status, void *stream);
 
+/* Semirings (+) . (x) of spmm_csr_semiring. */
+typedef enum {
+    SPMM_SEMIRING_PLUS_TIMES = 0, /* (+, x), identity 0: the ordinary product     */
+    SPMM_SEMIRING_MIN_PLUS = 1,   /* (min, +), identity +inf: shortest-path step  */
+    SPMM_SEMIRING_MAX_PLUS = 2,   /* (max, +), identity -inf: longest-path step   */
+    SPMM_SEMIRING_MAX_TIMES = 3   /* (max, x), identity -inf: most reliable path  */
+} spmm_semiring_t;
+
+/*
+ * C = A (+).(x) B over a semiring, float32 throughout: the GraphBLAS
+ * matrix-matrix product that Section 1 names as a use of SpMM.
+ * C[i][j] = (+) over the stored p of row i of (vals[p] (x) B[col_ind[p]][j]),
+ * starting from the identity of (+), so an empty row gives the identity.
+ * Both families (row split, merge based) and the selectors run unchanged;
+ * the accumulate, the in-CTA combine and the fix-up use (+) and (x), and the
+ * fix-up combines a split row's partial results in tile order as for the
+ * ordinary product.  min and max are fminf / fmaxf (a NaN operand loses to a
+ * number).  Arguments and workspace as in spmm_csr_ex (b_type float32);
+ * semiring outside spmm_semiring_t returns SPMM_ERR_INVALID_VALUE.
+ */
+int spmm_csr_semiring(int m, int k, int n, long long nnz, const int *row_ptr, const int *col_ind,
+                      const float *vals, const float *B, long long ldb, float *C, long long ldc, int semiring,
+                      int alg, const spmm_tuning_t *tuning, void *workspace, size_t workspace_bytes,
+                      int *d_status, void *stream);
+
 /*
  * Bytes of workspace spmm_csr_ex needs for these sizes.  0 for row split.
  * alg SPMM_ALG_AUTO is resolved with the heuristic first.  Returns 0 for

@@ -23,6 +23,9 @@ import threading
 
 ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300 = 0, 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
+SEMIRING_PLUS_TIMES, SEMIRING_MIN_PLUS, SEMIRING_MAX_PLUS, SEMIRING_MAX_TIMES = 0, 1, 2, 3
+SEMIRINGS = {"plus_times": SEMIRING_PLUS_TIMES, "min_plus": SEMIRING_MIN_PLUS, "max_plus": SEMIRING_MAX_PLUS,
+             "max_times": SEMIRING_MAX_TIMES}
 OK = 0
 ERR_INVALID_VALUE, ERR_ALLOC, ERR_LAUNCH, ERR_BAD_CSR, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE = range(1, 9)
 PAPER_THRESHOLD = 9.35  # Section 5.4
@@ -60,6 +63,7 @@ _SIGNATURES = {
     "spmm_csr_max_row_length": ([_i, _vp, ctypes.POINTER(_ll), _vp], _i),
     "spmm_csr": ([_i, _i, _i, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _vp], _i),
     "spmm_csr_ex": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _sz, _vp, _vp], _i),
+    "spmm_csr_semiring": ([_i, _i, _i, _ll, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _i, _TP, _vp, _sz, _vp, _vp], _i),
     "spmm_csr_workspace_size": ([_i, _i, _i, _ll, _i, _i, _TP], _sz),
     "spmm_merge_partition": ([_i, _ll, _vp, _i, _i, _vp, _vp], _i),
     "spmm_csr_host": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
@@ -177,6 +181,12 @@ def spmm_csr_noalloc(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type,
                                    alg, _tuning_ptr(tuning), d_status, stream)
 
 
+def spmm_csr_semiring(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, semiring, alg, tuning, workspace,
+                      workspace_bytes, d_status, stream) -> int:
+    return load().spmm_csr_semiring(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, semiring, alg,
+                                    _tuning_ptr(tuning), workspace, workspace_bytes, d_status, stream)
+
+
 def spmm_csr_static_scratch_bytes() -> int:
     return load().spmm_csr_static_scratch_bytes()
 
@@ -271,6 +281,35 @@ def spmm(row_ptr, col_ind, vals, B, alg="auto", out=None, out_dtype=None, nnz=No
                      out.data_ptr(), dtype_code(out.dtype), out.stride(0), alg_code(alg), tuning, ws_ptr, ws_bytes,
                      status.data_ptr() if status is not None else None, _stream_handle(stream))
     _check(st, "spmm_csr_ex")
+    return out
+
+
+def semiring_spmm(row_ptr, col_ind, vals, B, semiring, alg="auto", out=None, nnz=None, tuning=None, workspace=None,
+                  status=None, stream=None):
+    """C = A (+).(x) B over ``semiring`` (a name of SEMIRINGS or its code), float32
+    throughout; arguments as :func:`spmm`.  An empty row of A gives the identity of (+)."""
+    torch = _torch()
+    _require_cuda(row_ptr, col_ind, vals, B, out)
+    for t, name in ((vals, "vals"), (B, "B")):
+        if t.dtype != torch.float32:
+            raise TypeError(f"{name} must be float32 for a semiring product")
+    if row_ptr.dtype != torch.int32 or col_ind.dtype != torch.int32:
+        raise TypeError("row_ptr and col_ind must be int32")
+    if B.dim() != 2 or B.stride(1) != 1:
+        raise ValueError("B must be a row-major 2-D tensor")
+    sr = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+    m = row_ptr.numel() - 1
+    k, n = B.shape
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float32, device=B.device)
+    if out.dim() != 2 or out.shape != (m, n) or out.stride(1) != 1 or out.dtype != torch.float32:
+        raise ValueError("out must be a row-major float32 [m, n] tensor")
+    ws_ptr, ws_bytes = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None else (None, 0)
+    st = spmm_csr_semiring(m, k, n, -1 if nnz is None else int(nnz), row_ptr.data_ptr(), col_ind.data_ptr(),
+                           vals.data_ptr(), B.data_ptr(), B.stride(0), out.data_ptr(), out.stride(0), sr,
+                           alg_code(alg), tuning, ws_ptr, ws_bytes, status.data_ptr() if status is not None else None,
+                           _stream_handle(stream))
+    _check(st, "spmm_csr_semiring")
     return out
 
 

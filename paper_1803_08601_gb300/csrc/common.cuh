@@ -119,6 +119,52 @@ __device__ __forceinline__ void fma_raw(float (&acc)[VEC], float a, const Raw<T,
     }
 }
 
+// ------------------------------------------------------------------ semirings
+//
+// C = A (+).(x) B (the GraphBLAS matrix product named in Section 1).  Each tag
+// gives the identity of (+), (+) itself, and acc (+) (a (x) b).  PlusTimes is
+// the ordinary product; its padding lanes may add 0 * 0, the others must skip
+// padded terms (kZeroPadOk = false).
+struct PlusTimes {
+    static constexpr bool kZeroPadOk = true;
+    __device__ __forceinline__ static float identity() { return 0.0f; }
+    __device__ __forceinline__ static float add(float x, float y) { return x + y; }
+    __device__ __forceinline__ static float mul_add(float acc, float a, float b) { return fmaf(a, b, acc); }
+};
+struct MinPlus {
+    static constexpr bool kZeroPadOk = false;
+    __device__ __forceinline__ static float identity() { return __int_as_float(0x7f800000); }  // +inf
+    __device__ __forceinline__ static float add(float x, float y) { return fminf(x, y); }
+    __device__ __forceinline__ static float mul_add(float acc, float a, float b) { return fminf(acc, a + b); }
+};
+struct MaxPlus {
+    static constexpr bool kZeroPadOk = false;
+    __device__ __forceinline__ static float identity() { return __int_as_float(0xff800000); }  // -inf
+    __device__ __forceinline__ static float add(float x, float y) { return fmaxf(x, y); }
+    __device__ __forceinline__ static float mul_add(float acc, float a, float b) { return fmaxf(acc, a + b); }
+};
+struct MaxTimes {
+    static constexpr bool kZeroPadOk = false;
+    __device__ __forceinline__ static float identity() { return __int_as_float(0xff800000); }  // -inf
+    __device__ __forceinline__ static float add(float x, float y) { return fmaxf(x, y); }
+    __device__ __forceinline__ static float mul_add(float acc, float a, float b) { return fmaxf(acc, a * b); }
+};
+
+// acc[e] = acc[e] (+) (a (x) element e of r).
+template <typename SR, typename T, int VEC>
+__device__ __forceinline__ void accum_raw(float (&acc)[VEC], float a, const Raw<T, VEC>& r) {
+    if constexpr (SR::kZeroPadOk) {
+        fma_raw<T, VEC>(acc, a, r);
+    } else {
+        float b[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) b[e] = 0.0f;
+        fma_raw<T, VEC>(b, 1.0f, r);  // widen
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = SR::mul_add(acc[e], a, b[e]);
+    }
+}
+
 // Store VEC floats as TC at p (p aligned to VEC * sizeof(TC) when VEC > 1).
 template <typename TC, int VEC>
 __device__ __forceinline__ void store_vec(TC* p, const float (&v)[VEC]) {

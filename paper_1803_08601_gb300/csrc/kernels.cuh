@@ -47,7 +47,7 @@ struct RowSplitArgs {
 // do, but the lanes still join the warp's shuffles) computes the `slab`-th
 // W * VEC columns of C[row, :].  Every lane of the warp must call this the
 // same number of times.
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long row, int slab) {
     constexpr int U = kUnroll;
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
@@ -67,7 +67,7 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
     }
     float acc[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+    for (int e = 0; e < VEC; ++e) acc[e] = SR::identity();
 
     const int nb = (re - rs + BS - 1) / BS;
     const int nb_max = __reduce_max_sync(kFullMask, nb);
@@ -96,18 +96,21 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
                 bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+            for (int u = 0; u < U; ++u) {
+                if constexpr (SR::kZeroPadOk) fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+                else if (g * U + u < cnt) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+            }
         }
     }
     if (row < a.m && col_ok) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc);
 }
 
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
     constexpr int RPW = 32 / W;  // rows per warp
     const long long row =
         (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / W;
-    rowsplit_row<TV, TB, TC, VEC, W>(a, row, blockIdx.y);
+    rowsplit_row<TV, TB, TC, VEC, W, SR>(a, row, blockIdx.y);
 }
 
 // ============================================================================ merge path
@@ -291,7 +294,7 @@ __device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const Merge
 // barrier.  Of the tile as a whole, the partial sum of a row that began in an
 // earlier tile (head) and of the row left unfinished at its end (carry) go to
 // global memory for the fix-up pass.
-template <typename TV, typename TB, typename TC, int VEC, int W, int NT>
+template <typename TV, typename TB, typename TC, int VEC, int W, int NT, typename SR = PlusTimes>
 __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<TV, VEC, W, NT>& v, int item, int b) {
     using L = MergeSmem<TV, VEC, W, NT>;
     constexpr int U = kUnroll;
@@ -334,7 +337,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
     int first_row = -1;
     float acc[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+    for (int e = 0; e < VEC; ++e) acc[e] = SR::identity();
 
     auto emit = [&]() {
         if (first_row < 0) {
@@ -348,7 +351,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
             store_vec<TC, VEC>(C + (long long)row * a.ldc + col0, acc);
         }
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+        for (int e = 0; e < VEC; ++e) acc[e] = SR::identity();
         ++row;
         rend = row < r1 ? srp[row + 1] : INT_MAX;
     };
@@ -385,7 +388,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
                 if (j < cnt) {
                     const int p = base + j;
                     while (p >= rend) emit();  // rows (possibly empty) that end before nonzero p
-                    fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+                    accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
                 }
             }
         }
@@ -410,15 +413,15 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
         while (t >= 0 && v.carry_row()[t] == fr) --t;
         float sum[VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) sum[e] = 0.0f;
+        for (int e = 0; e < VEC; ++e) sum[e] = SR::identity();
         for (int u = t + 1; u < s; ++u) {
             const float* c = v.carry(u) + sl * VEC;
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) sum[e] += c[e];
+            for (int e = 0; e < VEC; ++e) sum[e] = SR::add(sum[e], c[e]);
         }
         const float* f = v.first(s) + sl * VEC;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) sum[e] += f[e];
+        for (int e = 0; e < VEC; ++e) sum[e] = SR::add(sum[e], f[e]);
         if (fr == r0 && head_exists) {
             float* h = a.head + (size_t)tile * a.n + col0;
 #pragma unroll
@@ -434,11 +437,11 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
         while (t > 0 && v.carry_row()[t - 1] == r1) --t;
         float sum[VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) sum[e] = 0.0f;
+        for (int e = 0; e < VEC; ++e) sum[e] = SR::identity();
         for (int u = t; u <= s; ++u) {
             const float* c = v.carry(u) + sl * VEC;
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) sum[e] += c[e];
+            for (int e = 0; e < VEC; ++e) sum[e] = SR::add(sum[e], c[e]);
         }
         float* cg = a.carry + (size_t)tile * a.n + col0;
 #pragma unroll
@@ -456,7 +459,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
 // is computed.  Every mbarrier wait is bounded: when one runs out the kernel
 // records SPMM_ERR_TIMEOUT, waits (bounded) for its copies still in flight
 // and returns.
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __device__ __forceinline__ void merge_kernel_body(const MergeArgs& a) {
     constexpr int NT = merge_cta_threads(W);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -471,7 +474,7 @@ __device__ __forceinline__ void merge_kernel_body(const MergeArgs& a) {
         for (; item < total; item += gridDim.x) {
             merge_load_plain<TV, VEC, W, NT>(a, v, item, 0);
             __syncthreads();
-            merge_tile<TV, TB, TC, VEC, W, NT>(a, v, item, 0);
+            merge_tile<TV, TB, TC, VEC, W, NT, SR>(a, v, item, 0);
             __syncthreads();
         }
         return;
@@ -504,21 +507,21 @@ __device__ __forceinline__ void merge_kernel_body(const MergeArgs& a) {
         }
         phase ^= 1u << b;
         pending &= ~(1u << b);
-        merge_tile<TV, TB, TC, VEC, W, NT>(a, v, item, b);
+        merge_tile<TV, TB, TC, VEC, W, NT, SR>(a, v, item, b);
         __syncthreads();
     }
 }
 
 // Narrow rows (W <= 8): 128-thread CTAs, six per SM.
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __global__ void __launch_bounds__(128, 6) merge_kernel_narrow(MergeArgs a) {
-    merge_kernel_body<TV, TB, TC, VEC, W>(a);
+    merge_kernel_body<TV, TB, TC, VEC, W, SR>(a);
 }
 
 // Wide rows (W >= 16): 256-thread CTAs.
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __global__ void __launch_bounds__(256) merge_kernel_wide(MergeArgs a) {
-    merge_kernel_body<TV, TB, TC, VEC, W>(a);
+    merge_kernel_body<TV, TB, TC, VEC, W, SR>(a);
 }
 
 // FIXCARRYOUT of Algorithm 1.  For every run of consecutive tiles whose
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(256) merge_kernel_wide(MergeArgs a) {
 // is finished by the tile right after the run, which left R's remaining
 // partial sum in head[]; C[R] = carries (in tile order) + head, rounded once.
 // One warp per tile (grid-stride); only run heads do work, lanes stride n.
-template <typename TC>
+template <typename TC, typename SR = PlusTimes>
 __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int* __restrict__ head_row,
                                    const float* __restrict__ carry, const float* __restrict__ head, int num_tiles,
                                    int n, TC* __restrict__ C, long long ldc, int* status) {
@@ -543,9 +546,9 @@ __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int*
             continue;
         }
         for (int c = lane; c < n; c += 32) {
-            float sum = 0.0f;
-            for (int t = i; t <= j; ++t) sum += carry[(size_t)t * n + c];
-            sum += head[(size_t)(j + 1) * n + c];
+            float sum = SR::identity();
+            for (int t = i; t <= j; ++t) sum = SR::add(sum, carry[(size_t)t * n + c]);
+            sum = SR::add(sum, head[(size_t)(j + 1) * n + c]);
             C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
         }
     }

@@ -3,6 +3,7 @@
 // unit (inst_*.cu) so the library builds in parallel.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.cuh"
@@ -24,11 +25,13 @@ extern std::atomic<long long> g_launches;
 using RowSplitFn = cudaError_t (*)(const RowSplitArgs&, const Shape&, cudaStream_t);
 using MergeFn = cudaError_t (*)(const MergeArgs&, const Shape&, int grid_cap, cudaStream_t);
 using MergeSmemFn = size_t (*)(const Shape&);
+using FixupFn = cudaError_t (*)(const MergeArgs&, cudaStream_t);
 
 struct Launchers {
     RowSplitFn rowsplit;
     MergeFn merge;
     MergeSmemFn merge_smem;
+    FixupFn fixup;
 };
 
 // defined in inst_*.cu
@@ -39,46 +42,48 @@ Launchers launchers_bf16_f16_f16();
 Launchers launchers_bf16_f16_f32();
 Launchers launchers_f16_f16_f16();
 Launchers launchers_f16_f16_f32();
+// float32 launchers of SPMM_SEMIRING_MIN_PLUS / MAX_PLUS / MAX_TIMES (inst_semiring.cu)
+const Launchers* find_semiring_launchers(int semiring);
 
 // ---------------------------------------------------------------------------- templates
 
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
 cudaError_t rowsplit_launch_one(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
     const long long rows_per_cta = kThreads / W;
     const long long gx = (a.m + rows_per_cta - 1) / rows_per_cta;
     if (gx > 0x7fffffffLL || s.slabs > 65535) return cudaErrorInvalidConfiguration;
-    rowsplit_kernel<TV, TB, TC, VEC, W><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a);
+    rowsplit_kernel<TV, TB, TC, VEC, W, SR><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
     return e;
 }
 
-template <typename TV, typename TB, typename TC, int VEC>
+template <typename TV, typename TB, typename TC, int VEC, typename SR>
 cudaError_t rowsplit_launch_vec(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
     switch (s.W) {
-        case 1: return rowsplit_launch_one<TV, TB, TC, VEC, 1>(a, s, st);
-        case 2: return rowsplit_launch_one<TV, TB, TC, VEC, 2>(a, s, st);
-        case 4: return rowsplit_launch_one<TV, TB, TC, VEC, 4>(a, s, st);
-        case 8: return rowsplit_launch_one<TV, TB, TC, VEC, 8>(a, s, st);
-        case 16: return rowsplit_launch_one<TV, TB, TC, VEC, 16>(a, s, st);
-        case 32: return rowsplit_launch_one<TV, TB, TC, VEC, 32>(a, s, st);
+        case 1: return rowsplit_launch_one<TV, TB, TC, VEC, 1, SR>(a, s, st);
+        case 2: return rowsplit_launch_one<TV, TB, TC, VEC, 2, SR>(a, s, st);
+        case 4: return rowsplit_launch_one<TV, TB, TC, VEC, 4, SR>(a, s, st);
+        case 8: return rowsplit_launch_one<TV, TB, TC, VEC, 8, SR>(a, s, st);
+        case 16: return rowsplit_launch_one<TV, TB, TC, VEC, 16, SR>(a, s, st);
+        case 32: return rowsplit_launch_one<TV, TB, TC, VEC, 32, SR>(a, s, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename TV, typename TB, typename TC>
+template <typename TV, typename TB, typename TC, typename SR>
 cudaError_t rowsplit_launch(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
     constexpr int V = Elem<TB>::kVec;
-    return s.vec == 1 ? rowsplit_launch_vec<TV, TB, TC, 1>(a, s, st) : rowsplit_launch_vec<TV, TB, TC, V>(a, s, st);
+    return s.vec == 1 ? rowsplit_launch_vec<TV, TB, TC, 1, SR>(a, s, st) : rowsplit_launch_vec<TV, TB, TC, V, SR>(a, s, st);
 }
 
-template <typename TV, typename TB, typename TC, int VEC, int W>
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
 cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
     constexpr int NT = merge_cta_threads(W);
     using L = MergeSmem<TV, VEC, W, NT>;
     auto kern = [] {
-        if constexpr (NT == 256) return merge_kernel_wide<TV, TB, TC, VEC, W>;
-        else return merge_kernel_narrow<TV, TB, TC, VEC, W>;
+        if constexpr (NT == 256) return merge_kernel_wide<TV, TB, TC, VEC, W, SR>;
+        else return merge_kernel_narrow<TV, TB, TC, VEC, W, SR>;
     }();
     static_assert(NT == 128 || NT == 256, "merge CTA shapes");
     const size_t smem = L::total(s.ips);
@@ -119,24 +124,45 @@ cudaError_t merge_launch_one(const MergeArgs& a, const Shape& s, int grid_cap, c
     return e;
 }
 
-template <typename TV, typename TB, typename TC, int VEC>
+template <typename TV, typename TB, typename TC, int VEC, typename SR>
 cudaError_t merge_launch_vec(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
     switch (s.W) {
-        case 1: return merge_launch_one<TV, TB, TC, VEC, 1>(a, s, grid_cap, st);
-        case 2: return merge_launch_one<TV, TB, TC, VEC, 2>(a, s, grid_cap, st);
-        case 4: return merge_launch_one<TV, TB, TC, VEC, 4>(a, s, grid_cap, st);
-        case 8: return merge_launch_one<TV, TB, TC, VEC, 8>(a, s, grid_cap, st);
-        case 16: return merge_launch_one<TV, TB, TC, VEC, 16>(a, s, grid_cap, st);
-        case 32: return merge_launch_one<TV, TB, TC, VEC, 32>(a, s, grid_cap, st);
+        case 1: return merge_launch_one<TV, TB, TC, VEC, 1, SR>(a, s, grid_cap, st);
+        case 2: return merge_launch_one<TV, TB, TC, VEC, 2, SR>(a, s, grid_cap, st);
+        case 4: return merge_launch_one<TV, TB, TC, VEC, 4, SR>(a, s, grid_cap, st);
+        case 8: return merge_launch_one<TV, TB, TC, VEC, 8, SR>(a, s, grid_cap, st);
+        case 16: return merge_launch_one<TV, TB, TC, VEC, 16, SR>(a, s, grid_cap, st);
+        case 32: return merge_launch_one<TV, TB, TC, VEC, 32, SR>(a, s, grid_cap, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename TV, typename TB, typename TC>
+template <typename TV, typename TB, typename TC, typename SR>
 cudaError_t merge_launch(const MergeArgs& a, const Shape& s, int grid_cap, cudaStream_t st) {
     constexpr int V = Elem<TB>::kVec;
-    return s.vec == 1 ? merge_launch_vec<TV, TB, TC, 1>(a, s, grid_cap, st)
-                      : merge_launch_vec<TV, TB, TC, V>(a, s, grid_cap, st);
+    return s.vec == 1 ? merge_launch_vec<TV, TB, TC, 1, SR>(a, s, grid_cap, st)
+                      : merge_launch_vec<TV, TB, TC, V, SR>(a, s, grid_cap, st);
+}
+
+// FIXCARRYOUT launch: a warp per tile (grid-stride), chained behind the merge
+// kernel with programmatic dependent launch.
+template <typename TC, typename SR>
+cudaError_t fixup_launch(const MergeArgs& ma, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(((long long)ma.num_tiles + 7) / 8, 152LL * 8));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, merge_fixup_kernel<TC, SR>, (const int*)ma.carry_row,
+                                       (const int*)ma.head_row, (const float*)ma.carry, (const float*)ma.head,
+                                       ma.num_tiles, ma.n, static_cast<TC*>(ma.C), ma.ldc, ma.status);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
 }
 
 template <typename TV, int VEC>
@@ -157,9 +183,10 @@ size_t merge_smem(const Shape& s) {
     return s.vec == 1 ? merge_smem_vec<TV, 1>(s) : merge_smem_vec<TV, V>(s);
 }
 
-template <typename TV, typename TB, typename TC>
+template <typename TV, typename TB, typename TC, typename SR = PlusTimes>
 Launchers make_launchers() {
-    return Launchers{&rowsplit_launch<TV, TB, TC>, &merge_launch<TV, TB, TC>, &merge_smem<TV, TB, TC>};
+    return Launchers{&rowsplit_launch<TV, TB, TC, SR>, &merge_launch<TV, TB, TC, SR>, &merge_smem<TV, TB, TC>,
+                     &fixup_launch<TC, SR>};
 }
 
 }  // namespace spmm

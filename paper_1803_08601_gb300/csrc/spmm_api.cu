@@ -14,6 +14,11 @@ namespace spmm {
 
 std::atomic<long long> g_launches{0};
 
+int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind,
+             const void* vals, int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type,
+             long long ldc, int alg, const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes,
+             int* d_status, void* stream);
+
 // Merge-path tiles (Section 4.2): the path that merges the row end offsets
 // row_ptr[1..m] with the nonzero indices 0..nnz-1 is cut into tiles of equal
 // length (rows + nonzeros).
@@ -395,9 +400,31 @@ int spmm_merge_partition(int m, long long nnz, const int* row_ptr, int items_per
 int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
                 int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
                 const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes, int* d_status, void* stream) {
+    return spmm::run_spmm(find_launchers(vals_type, b_type, c_type), m, k, n, nnz, row_ptr, col_ind, vals, vals_type,
+                          B, b_type, ldb, C, c_type, ldc, alg, tuning, workspace, workspace_bytes, d_status, stream);
+}
+
+int spmm_csr_semiring(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const float* vals,
+                      const float* B, long long ldb, float* C, long long ldc, int semiring, int alg,
+                      const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes, int* d_status,
+                      void* stream) {
+    if (semiring < SPMM_SEMIRING_PLUS_TIMES || semiring > SPMM_SEMIRING_MAX_TIMES) return SPMM_ERR_INVALID_VALUE;
+    const Launchers* L = semiring == SPMM_SEMIRING_PLUS_TIMES ? find_launchers(SPMM_F32, SPMM_F32, SPMM_F32)
+                                                              : spmm::find_semiring_launchers(semiring);
+    return spmm::run_spmm(L, m, k, n, nnz, row_ptr, col_ind, vals, SPMM_F32, B, SPMM_F32, ldb, C, SPMM_F32, ldc, alg,
+                          tuning, workspace, workspace_bytes, d_status, stream);
+}
+
+}  // extern "C"
+
+namespace spmm {
+
+int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind,
+             const void* vals, int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type,
+             long long ldc, int alg, const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes,
+             int* d_status, void* stream) {
     int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
     if (st != SPMM_OK) return st;
-    const Launchers* L = find_launchers(vals_type, b_type, c_type);
     if (!L) return SPMM_ERR_UNSUPPORTED;
     if (m == 0 || n == 0) return SPMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -468,35 +495,17 @@ int spmm_csr_ex(int m, int k, int n, long long nnz, const int* row_ptr, const in
     st = spmm_merge_partition(m, nnz, row_ptr, ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
                               stream);
     if (st == SPMM_OK) st = cuda_status(L->merge(ma, shape, sm_count(), s));
-    if (st == SPMM_OK && lay.num_tiles > 1) {
-        auto fix = [&](auto* c) {
-            using TC = std::remove_pointer_t<decltype(c)>;
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)std::min<long long>(((long long)lay.num_tiles + 7) / 8, 152LL * 8));
-            cfg.blockDim = dim3(256);
-            cfg.stream = s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-            attr[0].val.programmaticStreamSerializationAllowed = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            cudaLaunchKernelEx(&cfg, merge_fixup_kernel<TC>, (const int*)ma.carry_row, (const int*)ma.head_row,
-                               (const float*)ma.carry, (const float*)ma.head, lay.num_tiles, n, static_cast<TC*>(C),
-                               ldc, d_status);
-        };
-        if (c_type == SPMM_F32) fix(static_cast<float*>(nullptr));
-        else if (c_type == SPMM_BF16) fix(static_cast<__nv_bfloat16*>(nullptr));
-        else fix(static_cast<__half*>(nullptr));
-        const cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
-        st = cuda_status(e);
-    }
+    if (st == SPMM_OK && lay.num_tiles > 1) st = cuda_status(L->fixup(ma, s));
     if (own) {
         const cudaError_t e = cudaFreeAsync(ws, s);
         if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
     }
     return st;
 }
+
+}  // namespace spmm
+
+extern "C" {
 
 int spmm_csr(int m, int k, int n, const int* row_ptr, const int* col_ind, const float* vals, const float* B,
              long long ldb, float* C, long long ldc, int alg, void* stream) {

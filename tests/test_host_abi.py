@@ -104,6 +104,26 @@ def test_argument_checks_return_before_any_device_work(lib):
     assert pkg.spmm_debug_bounded_wait(None, 1000, None) == pkg.ERR_INVALID_VALUE
 
 
+def test_semiring_argument_checks(lib):
+    good = dict(m=4, k=4, n=4, nnz=4, row_ptr=8, col_ind=16, vals=32, B=64, ldb=4, C=128, ldc=4,
+                semiring=pkg.SEMIRING_MIN_PLUS, alg=0, tuning=None, workspace=None, workspace_bytes=0, d_status=None,
+                stream=None)
+
+    def call(**kw):
+        a = dict(good)
+        a.update(kw)
+        return pkg.spmm_csr_semiring(*a.values())
+
+    assert call(semiring=4) == pkg.ERR_INVALID_VALUE
+    assert call(semiring=-1) == pkg.ERR_INVALID_VALUE
+    assert call(ldc=3) == pkg.ERR_INVALID_VALUE
+    assert call(alg=9) == pkg.ERR_INVALID_VALUE
+    for sr in pkg.SEMIRINGS.values():
+        assert call(semiring=sr, m=0) == pkg.OK
+        assert call(semiring=sr, n=0) == pkg.OK
+    assert pkg.SEMIRINGS == oracle.SEMIRINGS  # same codes on both sides of the ABI
+
+
 def test_workspace_size(lib):
     F = pkg.F32
     assert pkg.spmm_csr_workspace_size(1000, 1000, 64, 16000, pkg.ALG_ROW_SPLIT, F) == 0
