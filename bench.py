@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--forms", default="precision,backward,batched",
                    help="comma list of growth forms measured after the headline (empty: none)")
     p.add_argument("--batched-count", type=int, default=2048, help="matrices in the batched form")
+    p.add_argument("--ingest-ncu", default=None, metavar="CSV",
+                   help="instead of the benchmark: turn the ncu CSV of the traffic capture (the command recorded in "
+                        "profiles/merge_kernel_power_law_1M_dram.json, with --print-units base) into that JSON")
     p.add_argument("--sweep", default=None, choices=["aspect", "density"],
                    help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
                         "n = 64) or the density sweep against dense GEMM (100k x 100k, n = 64); JSON line per point")
@@ -108,27 +111,101 @@ def compulsory_bytes(m, nnz, k, n, s_v=4, s_b=4, s_c=4):
     return (m + 1) * 4 + nnz * (4 + s_v) + k * n * s_b + m * n * s_c
 
 
-def measured_traffic(kernel, label, ns):
-    """DRAM bytes (read + write) of the dominant kernel summed over the step's widths, from the
-    committed ncu capture in profiles/, or None when the kernel sources changed since."""
+TRAFFIC_SOURCES = ["paper_1803_08601_gb300/csrc/kernels.cuh", "paper_1803_08601_gb300/csrc/common.cuh"]
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "merge_kernel_power_law_1M_dram.json")
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_sector_hit_rate.pct,"
+                   "gpu__time_duration.sum --print-units base --clock-control none -k regex:merge_kernel -s 12 -c 4 "
+                   "--csv --log-file <CSV> python bench.py --steps 1 --warmup 3 --no-extras --forms= --no-clocks")
+
+
+def sources_sha256(paths):
     import hashlib
 
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def load_capture(kernel, label):
+    """The committed ncu capture of the dominant kernel on this workload, or (None, why)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_power_law_1M_dram.json")
     if label != "power_law_1Mx1M_mean16_cap1e5" or not os.path.exists(path):
         return None, "no capture for this kernel and workload"
     with open(path) as f:
         cap = json.load(f)
-    h = hashlib.sha256()
-    for p in cap["sources"]:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != cap["sources_sha256"]:
+    if sources_sha256(cap["sources"]) != cap["sources_sha256"]:
         return None, "kernel sources changed since the ncu capture"
+    return cap, os.path.basename(path)
+
+
+def measured_traffic(kernel, label, ns):
+    """DRAM bytes (read + write) of the dominant kernel summed over the step's widths, from the
+    committed ncu capture in profiles/, or None when the kernel sources changed since."""
+    cap, note = load_capture(kernel, label)
+    if cap is None:
+        return None, note
     if not all(str(n) in cap["per_n"] for n in ns):
         return None, "capture lacks some widths"
     t = sum(cap["per_n"][str(n)]["dram_read_bytes"] + cap["per_n"][str(n)]["dram_write_bytes"] for n in ns)
     return t, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch per width, summed over the "
-               f"step's widths {ns} (profiles/{os.path.basename(path)}); same units as achieved x duration")
+               f"step's widths {ns} (profiles/{note}); same units as achieved x duration")
+
+
+def gather_aware(kernel, label, m, nnz, k, ns, mean_call, peak, l2_bytes, s_b=4):
+    """The gather-aware bound: A + C + nnz n s_B (1 - h), h the L2 hit rate of the B gathers.
+    h is the capture's lts__t_sector_hit_rate (all L2 sectors of the launch, dominated by the
+    gathers) while the capture is current, else the uniform-column model min(1, L2 / |B|)."""
+    cap, note = load_capture(kernel, label)
+    per_n, total_bytes, total_ms = {}, 0.0, 0.0
+    for n in ns:
+        if cap is not None and str(n) in cap["per_n"]:
+            h, src = cap["per_n"][str(n)]["l2_sector_hit_pct"] / 100.0, f"ncu lts__t_sector_hit_rate ({note})"
+        else:
+            h, src = min(1.0, l2_bytes / float(k * n * s_b)), "model min(1, L2 / |B|)"
+        b = (m + 1) * 4 + nnz * 8 + m * n * 4 + nnz * n * s_b * (1.0 - h)
+        t_min = b / (peak * 1e9) * 1e3
+        per_n[str(n)] = {"h": h, "h_source": src, "bytes": b, "t_min_ms": t_min, "frac": t_min / mean_call[n]}
+        total_bytes += b
+        total_ms += mean_call[n]
+    return {"formula": "(m+1)*4 + nnz*8 + m*n*4 + nnz*n*4*(1-h) per call", "bytes": total_bytes,
+            "frac": total_bytes / (peak * 1e9) * 1e3 / total_ms, "per_n": per_n}
+
+
+def ingest_ncu(csv_path, out_path=TRAFFIC_JSON):
+    """Write the traffic JSON from the ncu CSV of TRAFFIC_COMMAND: the four merge_kernel launches
+    of the timed step, in the step's width order 8, 32, 64, 128."""
+    import csv
+
+    launches = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(line for line in f if line.startswith('"'))]
+    head = rows[0]
+    col = {name: head.index(name) for name in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    for r in rows[1:]:
+        d = launches.setdefault(int(r[col["ID"]]), {"kernel": r[col["Kernel Name"]]})
+        d[r[col["Metric Name"]]] = (float(r[col["Metric Value"]].replace(",", "")), r[col["Metric Unit"]])
+    ids = sorted(launches)
+    if len(ids) != 4:
+        raise SystemExit(f"expected 4 captured launches, found {len(ids)}")
+    per_n = {}
+    for n, i in zip((8, 32, 64, 128), ids):
+        d = launches[i]
+        assert d["dram__bytes_read.sum"][1] == "byte" and d["gpu__time_duration.sum"][1] == "ns", d
+        per_n[str(n)] = {"dram_read_bytes": int(d["dram__bytes_read.sum"][0]),
+                         "dram_write_bytes": int(d["dram__bytes_write.sum"][0]),
+                         "duration_ns": int(d["gpu__time_duration.sum"][0]),
+                         "l2_sector_hit_pct": round(d["lts__t_sector_hit_rate.pct"][0], 2),
+                         "kernel": d["kernel"]}
+    out = {"kernel": "merge_kernel (float32, 16-byte vectors; W = n/4 lanes per row, or n/8 with two slabs)",
+           "workload": "power_law_1Mx1M_mean16_cap1e5", "command": TRAFFIC_COMMAND,
+           "sources": TRAFFIC_SOURCES, "sources_sha256": sources_sha256(TRAFFIC_SOURCES), "per_n": per_n}
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
+    return 0
 
 
 def peaks():
@@ -270,6 +347,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ingest_ncu:
+        return ingest_ncu(args.ingest_ncu)
     if args.sweep:
         return run_sweep(args)
     import torch
@@ -359,7 +438,9 @@ def main():
                 "algorithmic_bytes": "compulsory: (m+1)*4 + nnz*8 + k*n*4 + m*n*4 per call, summed over n",
                 "per_n": {str(n): {"ms": mean_call[n], "gb_s": comp[n] / (mean_call[n] * 1e-3) / 1e9,
                                    "gflops": 2.0 * nnz * n / (mean_call[n] * 1e-3) / 1e9,
-                                   "alg": "merge" if alg_of[n] == pkg.ALG_MERGE else "row_split"} for n in ns}}
+                                   "alg": "merge" if alg_of[n] == pkg.ALG_MERGE else "row_split"} for n in ns},
+                "gather_aware": gather_aware(dom_alg[fam], label, m, nnz, k, fam_ns, mean_call, peak, l2),
+                "l2_bytes": l2}
 
     line = {"metric": "SpMM GFLOP/s (2*nnz*n/t)", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
