@@ -60,9 +60,10 @@ def parse():
     p.add_argument("--ingest-ncu", default=None, metavar="CSV",
                    help="instead of the benchmark: turn the ncu CSV of the traffic capture (the command recorded in "
                         "profiles/merge_kernel_power_law_1M_dram.json, with --print-units base) into that JSON")
-    p.add_argument("--sweep", default=None, choices=["aspect", "density"],
+    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv"],
                    help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
-                        "n = 64) or the density sweep against dense GEMM (100k x 100k, n = 64); JSON line per point")
+                        "n = 64), the density sweep against dense GEMM (100k x 100k, n = 64) or SpMV (n = 1) on "
+                        "five matrices against cuSPARSE through torch; JSON line per point")
     return p.parse_args()
 
 
@@ -697,6 +698,8 @@ def run_sweep(args):
             print(json.dumps(row), flush=True)
             del rp, ci, v, B, C, ws
             torch.cuda.empty_cache()
+    elif args.sweep == "spmv":
+        run_spmv_sweep(pkg, torch, dev, flush, stream, reps)
     else:
         # fixed fraction of nonzeros per row of a 100k x 100k matrix vs dense GEMM (the paper's Fig. 7)
         mk = 100_000
@@ -725,6 +728,59 @@ def run_sweep(args):
             del rp, ci, v, C, dense
             torch.cuda.empty_cache()
     return 0
+
+
+def run_spmv_sweep(pkg, torch, dev, flush, stream, reps):
+    """y = A x (n = 1): both families, both selectors, and cuSPARSE's CSR SpMV through torch as a
+    library reference, on the compulsory-bytes roofline (m+1)*4 + nnz*8 + k*4 + m*4."""
+    peak, peak_src = peaks()
+    mats = [("power_law_1Mx1M_mean16_cap1e5", lambda: gen.workload_power_law()),
+            ("uniform_1Mx1M_16", lambda: gen.uniform_rows(1_000_000, 1_000_000, 16, gen.SEED_BASE + 80)),
+            ("uniform_4Mx4M_4", lambda: gen.uniform_rows(4_000_000, 4_000_000, 4, gen.SEED_BASE + 81)),
+            ("uniform_2Mx2M_32", lambda: gen.uniform_rows(2_000_000, 2_000_000, 32, gen.SEED_BASE + 82)),
+            ("uniform_250kx250k_64", lambda: gen.uniform_rows(250_000, 250_000, 64, gen.SEED_BASE + 83))]
+    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    for label, make in mats:
+        a = make()
+        m, k, nnz = a.m, a.k, a.nnz
+        rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
+        lmax = int(np.diff(a.row_ptr).max()) if m else 0
+        del a
+        x = torch.randn(k, 1, device=dev, generator=torch.Generator(device=dev).manual_seed(9))
+        y = torch.empty(m, 1, device=dev)
+        ws = torch.empty(max(256, pkg.workspace_size(m, k, 1, nnz, "merge")), dtype=torch.uint8, device=dev)
+        comp = (m + 1) * 4 + nnz * 8 + k * 4 + m * 4
+        row = {"sweep": "spmv", "matrix": label, "m": m, "k": k, "nnz": nnz, "max_row": lmax,
+               "compulsory_bytes": comp, "peak_gbs": peak, "peak_source": peak_src,
+               "paper_pick": name[pkg.spmm_select_alg(m, nnz, 0.0)],
+               "gb300_pick": name[pkg.spmm_select_alg_gb300(m, nnz, lmax, 1, pkg.F32)]}
+        tun = {"max_row_len": lmax}
+        ref = None
+        for alg in ("row_split", "merge", "auto", "auto_gb300"):
+            r = reps if not (alg in ("row_split", "auto") and lmax > 10_000) else 1
+            t = _time(torch, lambda: pkg.spmm(rp, ci, v, x, alg=alg, out=y, nnz=nnz, workspace=ws, tuning=tun),
+                      flush, stream, r)
+            if ref is None:
+                ref = y.clone()
+            row[alg] = {"ms": t, "gb_s": comp / t / 1e6, "frac": comp / t / 1e6 / peak,
+                        "gflops": 2.0 * nnz / t / 1e6, "max_abs_diff_vs_row_split": float((y - ref).abs().max())}
+        # the same nnz random 4-byte reads of x with no reduction: the gather-request ceiling
+        xf = x.view(-1)
+        g = torch.empty(nnz, device=dev)
+        t = _time(torch, lambda: torch.index_select(xf, 0, ci, out=g), flush, stream, reps)
+        row["gather_only_index_select"] = {"ms": t, "g_gathers_per_s": nnz / t / 1e6}
+        del g
+        try:
+            A = torch.sparse_csr_tensor(rp, ci, v, size=(m, k))
+            xv = x.view(-1)
+            t = _time(torch, lambda: torch.mv(A, xv), flush, stream, reps)
+            row["cusparse_via_torch"] = {"ms": t, "gb_s": comp / t / 1e6, "frac": comp / t / 1e6 / peak,
+                                         "max_abs_diff_vs_row_split": float((torch.mv(A, xv) - ref.view(-1)).abs().max())}
+        except Exception as e:  # library reference only; the sweep stands without it
+            row["cusparse_via_torch"] = {"unavailable": str(e).splitlines()[0][:200]}
+        print(json.dumps(row), flush=True)
+        del rp, ci, v, x, y, ws
+        torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":

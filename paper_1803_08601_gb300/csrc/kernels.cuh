@@ -554,4 +554,187 @@ __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int*
     }
 }
 
+// ============================================================================ SpMV (n = 1)
+//
+// Both families specialised for one dense column, y = A x (the SpMV case the
+// paper contrasts with SpMM in Section 3 and Table 1).  With n = 1 the lane
+// groups above shrink to one lane per row reading its row's nonzeros alone,
+// and every merge item costs a whole walk step for one 4-byte gather; here
+// the nonzeros are spread over the lanes instead.
+
+// Row split: G lanes per row stride over the row's nonzeros, so a warp reads
+// col_ind / vals in runs of G consecutive entries; four independent gathers
+// of x are in flight per lane; a shuffle reduction over the G lanes finishes
+// the row.  G = 1 is the thread-per-row form.
+template <typename TV, typename TB, typename TC, int G, typename SR = PlusTimes>
+__global__ void __launch_bounds__(kThreads) spmv_rowsplit_kernel(RowSplitArgs a) {
+    static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "lanes per row");
+    const long long row = (long long)blockIdx.x * (kThreads / G) + threadIdx.x / G;
+    const int lane = threadIdx.x & (G - 1);
+    const int* __restrict__ col = a.col_ind;
+    const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
+    const TB* __restrict__ x = static_cast<const TB*>(a.B);
+    float acc = SR::identity();
+    if (row < a.m) {
+        const int re = __ldg(a.row_ptr + row + 1);
+        int p = __ldg(a.row_ptr + row) + lane;
+        for (; p + 3 * G < re; p += 4 * G) {
+            int c[4];
+            float v[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldg(col + p + u * G);
+                v[u] = load_f(vals + p + u * G);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = load_f(x + (long long)c[u] * a.ldb);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc = SR::mul_add(acc, v[u], b[u]);
+        }
+        for (; p < re; p += G) acc = SR::mul_add(acc, load_f(vals + p), load_f(x + (long long)__ldg(col + p) * a.ldb));
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) acc = SR::add(acc, __shfl_xor_sync(kFullMask, acc, off, G));
+    }
+    if (lane == 0 && row < a.m) static_cast<TC*>(a.C)[row * a.ldc] = Elem<TC>::from_f(acc);
+}
+
+// Merge based: one CTA per merge-path tile of kThreads * T items (the
+// partition kernel's limits).  Every product val[p] (x) x[col[p]] of the tile
+// is gathered first, all loads independent and coalesced over the CTA, into
+// shared memory together with the row end offsets of the tile's rows; then
+// each thread walks its T items of the path over shared memory only.  A
+// thread's first finished row adds the carries of the threads before it that
+// worked on the same row; the tile's head and carry go to the fix-up as in
+// the SpMM kernel (same layout with n = 1).
+constexpr int kSpmvItems = 8;  // default merge items per thread
+
+template <typename TV, typename TB, typename TC, int T, typename SR = PlusTimes>
+__global__ void __launch_bounds__(kThreads) spmv_merge_kernel(MergeArgs a) {
+    constexpr int kTile = kThreads * T;
+    __shared__ float s_prod[kTile];
+    __shared__ int s_end[kTile];
+    __shared__ float s_carry[kThreads];
+    __shared__ int s_carry_row[kThreads];
+    __shared__ float s_warp_run[kThreads / 32];
+    __shared__ int s_warp_key[kThreads / 32], s_warp_first_key[kThreads / 32];
+    pdl_wait();               // the partition (launched just before) has finished writing limits
+    pdl_launch_dependents();  // the fix-up may be scheduled; it waits for this grid to finish
+    const int tile = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int2 lo = a.limits[tile], hi = a.limits[tile + 1];
+    const int r0 = lo.x, z0 = lo.y, r1 = hi.x, z1 = hi.y;
+    const int nr = r1 - r0, nz = z1 - z0, items = nr + nz;
+    const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
+    const TB* __restrict__ x = static_cast<const TB*>(a.B);
+    TC* __restrict__ y = static_cast<TC*>(a.C);
+
+    {
+        int c[T];
+        float v[T], b[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int i = tid + u * kThreads;
+            c[u] = i < nz ? __ldg(a.col_ind + z0 + i) : 0;
+            v[u] = i < nz ? load_f(vals + z0 + i) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u)
+            b[u] = tid + u * kThreads < nz ? load_f(x + (long long)c[u] * a.ldb) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int i = tid + u * kThreads;
+            if (i < nz) s_prod[i] = SR::mul_add(SR::identity(), v[u], b[u]);
+        }
+        for (int i = tid; i < nr; i += kThreads) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i);
+    }
+    __syncthreads();
+
+    // this thread's share of the tile's path: the first row end not taken
+    // before diagonal d (row ends go first on ties, as in the partition)
+    auto search = [&](int d) {
+        int l = d - nz > 0 ? d - nz : 0, h = d < nr ? d : nr;
+        while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (s_end[mid] <= z0 + d - mid - 1) l = mid + 1;
+            else h = mid;
+        }
+        return l;
+    };
+    const int ds = min(tid * T, items), de = min(ds + T, items);
+    int ri = search(ds);
+    int zi = ds - ri;
+    int rend = ri < nr ? s_end[ri] - z0 : INT_MAX;  // tile-local end of the current row
+    float acc = SR::identity();
+    int first = -1;
+    float first_val = SR::identity();
+    for (int d = ds; d < de; ++d) {
+        if (zi >= rend) {  // row r0 + ri ends here
+            if (first < 0) {
+                first = ri;
+                first_val = acc;
+            } else {
+                y[(long long)(r0 + ri) * a.ldc] = Elem<TC>::from_f(acc);
+            }
+            acc = SR::identity();
+            ++ri;
+            rend = ri < nr ? s_end[ri] - z0 : INT_MAX;
+        } else {
+            acc = SR::add(acc, s_prod[zi]);
+            ++zi;
+        }
+    }
+    // Carry rows do not decrease with the thread index, so the threads that
+    // carry one row are consecutive.  A keyed inclusive scan over the threads
+    // (in-warp by shuffles, across warps from the warps' last values) gives
+    // each thread the carries of its own run up to itself.
+    const int key = r0 + ri;
+    const int lane = tid & 31, warp = tid >> 5;
+    float run = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float v = __shfl_up_sync(kFullMask, run, off);
+        const int k = __shfl_up_sync(kFullMask, key, off);
+        if (lane >= off && k == key) run = SR::add(v, run);
+    }
+    if (lane == 31) {
+        s_warp_run[warp] = run;
+        s_warp_key[warp] = key;
+    }
+    if (lane == 0) s_warp_first_key[warp] = key;
+    __syncthreads();
+    // carries of earlier warps in the same run
+    auto from_earlier_warps = [&](int k, int w) {
+        float sum = SR::identity();
+        for (int u = w - 1; u >= 0 && s_warp_key[u] == k; --u) {
+            sum = SR::add(s_warp_run[u], sum);
+            if (s_warp_first_key[u] != k) break;  // the run starts inside warp u
+        }
+        return sum;
+    };
+    // inclusive run of this thread's carry: earlier warps, then this warp
+    const bool lane0_in_run = __shfl_sync(kFullMask, key, 0) == key;
+    float inclusive = run;
+    if (lane0_in_run) inclusive = SR::add(from_earlier_warps(key, warp), run);
+    s_carry[tid] = inclusive;
+    s_carry_row[tid] = key;
+    __syncthreads();
+
+    const bool head_exists = nr > 0 && __ldg(a.row_ptr + r0) < z0;  // row r0 began in an earlier tile, ends here
+    if (first >= 0) {
+        const int fr = r0 + first;
+        float sum = first_val;
+        if (tid > 0 && s_carry_row[tid - 1] == fr) sum = SR::add(s_carry[tid - 1], sum);
+        if (fr == r0 && head_exists) a.head[tile] = sum;
+        else y[(long long)fr * a.ldc] = Elem<TC>::from_f(sum);
+    }
+    if (tid == kThreads - 1) {
+        const bool carry_exists = r1 < a.m && z1 > __ldg(a.row_ptr + r1);  // row r1 began here, ends later
+        if (carry_exists) a.carry[tile] = s_carry[tid];  // the last thread's key is r1
+        a.carry_row[tile] = carry_exists ? r1 : -1;
+        a.head_row[tile] = head_exists ? r0 : -1;
+    }
+}
+
 }  // namespace spmm

@@ -26,12 +26,16 @@ using RowSplitFn = cudaError_t (*)(const RowSplitArgs&, const Shape&, cudaStream
 using MergeFn = cudaError_t (*)(const MergeArgs&, const Shape&, int grid_cap, cudaStream_t);
 using MergeSmemFn = size_t (*)(const Shape&);
 using FixupFn = cudaError_t (*)(const MergeArgs&, cudaStream_t);
+using SpmvRowSplitFn = cudaError_t (*)(const RowSplitArgs&, int lanes, cudaStream_t);
+using SpmvMergeFn = cudaError_t (*)(const MergeArgs&, int items_per_thread, cudaStream_t);
 
 struct Launchers {
     RowSplitFn rowsplit;
     MergeFn merge;
     MergeSmemFn merge_smem;
     FixupFn fixup;
+    SpmvRowSplitFn spmv_rowsplit;  // n = 1
+    SpmvMergeFn spmv_merge;        // n = 1, tiles of kThreads * items_per_thread items (4, 8 or 16)
 };
 
 // defined in inst_*.cu
@@ -165,6 +169,56 @@ cudaError_t fixup_launch(const MergeArgs& ma, cudaStream_t st) {
     return e;
 }
 
+template <typename TV, typename TB, typename TC, int G, typename SR>
+cudaError_t spmv_rowsplit_one(const RowSplitArgs& a, cudaStream_t st) {
+    const long long rows_per_cta = kThreads / G;
+    const long long gx = (a.m + rows_per_cta - 1) / rows_per_cta;
+    if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    spmv_rowsplit_kernel<TV, TB, TC, G, SR><<<(unsigned)gx, kThreads, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+template <typename TV, typename TB, typename TC, typename SR>
+cudaError_t spmv_rowsplit_launch(const RowSplitArgs& a, int lanes, cudaStream_t st) {
+    switch (lanes) {
+        case 1: return spmv_rowsplit_one<TV, TB, TC, 1, SR>(a, st);
+        case 2: return spmv_rowsplit_one<TV, TB, TC, 2, SR>(a, st);
+        case 4: return spmv_rowsplit_one<TV, TB, TC, 4, SR>(a, st);
+        case 8: return spmv_rowsplit_one<TV, TB, TC, 8, SR>(a, st);
+        case 16: return spmv_rowsplit_one<TV, TB, TC, 16, SR>(a, st);
+        case 32: return spmv_rowsplit_one<TV, TB, TC, 32, SR>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// One CTA per tile, chained behind the partition with programmatic dependent launch.
+template <typename TV, typename TB, typename TC, typename SR>
+cudaError_t spmv_merge_launch(const MergeArgs& a, int items_per_thread, cudaStream_t st) {
+    if (a.num_tiles < 1) return cudaSuccess;
+    void (*kern)(MergeArgs) = nullptr;
+    switch (items_per_thread) {
+        case 4: kern = spmv_merge_kernel<TV, TB, TC, 4, SR>; break;
+        case 8: kern = spmv_merge_kernel<TV, TB, TC, 8, SR>; break;
+        case 16: kern = spmv_merge_kernel<TV, TB, TC, 16, SR>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.num_tiles);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
 template <typename TV, int VEC>
 size_t merge_smem_vec(const Shape& s) {
     switch (s.W) {
@@ -186,7 +240,7 @@ size_t merge_smem(const Shape& s) {
 template <typename TV, typename TB, typename TC, typename SR = PlusTimes>
 Launchers make_launchers() {
     return Launchers{&rowsplit_launch<TV, TB, TC, SR>, &merge_launch<TV, TB, TC, SR>, &merge_smem<TV, TB, TC>,
-                     &fixup_launch<TC, SR>};
+                     &fixup_launch<TC, SR>, &spmv_rowsplit_launch<TV, TB, TC, SR>, &spmv_merge_launch<TV, TB, TC, SR>};
 }
 
 }  // namespace spmm

@@ -188,9 +188,8 @@ struct MergeLayout {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
+MergeLayout merge_layout_items(int m, long long nnz, int n, long long ipt) {
     MergeLayout L{};
-    const long long ipt = (long long)(merge_cta_threads(s.W) / s.W) * s.ips;
     const long long total = (long long)m + nnz;
     L.num_tiles = (int)((total + ipt - 1) / ipt);
     size_t off = 0;
@@ -206,6 +205,28 @@ MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
     off = align256(off + (size_t)L.num_tiles * n * 4);
     L.total = off;
     return L;
+}
+
+MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
+    return merge_layout_items(m, nnz, n, (long long)(merge_cta_threads(s.W) / s.W) * s.ips);
+}
+
+// Lanes per row of the SpMV row split: the power of two at or below a sixth
+// of the mean row length, at most 8 (measured on GB300 over mean lengths 2 to
+// 1000: fewer lanes per row, so more rows per warp, keep more independent
+// gathers in flight than one lane per nonzero does).
+int spmv_lanes(int m, long long nnz) {
+    const double d = m > 0 ? (double)nnz / m : 0.0;
+    int g = 1;
+    while (g < 8 && 12.0 * g <= d) g <<= 1;
+    return g;
+}
+
+// Items per thread of the SpMV merge kernel: 4, 8 (default) or 16, the
+// largest not above the requested items_per_subwarp.
+int spmv_items(const spmm_tuning_t* t) {
+    const int r = (t && t->items_per_subwarp > 0) ? t->items_per_subwarp : kSpmvItems;
+    return r >= 16 ? 16 : r >= 8 ? 8 : 4;
 }
 
 int sm_count() {
@@ -380,6 +401,10 @@ size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int 
             if (need > best) best = need;
         }
     }
+    if (n == 1) {  // the SpMV form's tiles
+        const size_t need = merge_layout_items(m, nnz, n, (long long)kThreads * spmv_items(tuning)).total;
+        if (need > best) best = need;
+    }
     return best;
 }
 
@@ -445,16 +470,25 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
     if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
     if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
+    const bool spmv = n == 1;  // y = A x: the SpMV forms of both families
     if (a == SPMM_ALG_ROW_SPLIT) {
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
+        if (spmv)
+            return cuda_status(
+                L->spmv_rowsplit(ra, t_eff.lanes_per_row > 0 ? t_eff.lanes_per_row : spmv_lanes(m, nnz), s));
         return cuda_status(L->rowsplit(ra, shape, s));
     }
 
-    // merge based: partition, compute, fix-up.  Tiles are capped so that the
-    // double-buffered staging fits the shared memory of one CTA.
-    clamp_tile(&shape, dtype_size(vals_type));
-    if (L->merge_smem(shape) > kMaxSmem) return SPMM_ERR_INVALID_VALUE;
-    const MergeLayout lay = merge_layout(m, nnz, n, shape);
+    // merge based: partition, compute, fix-up.  SpMM tiles are capped so that
+    // the double-buffered staging fits the shared memory of one CTA.
+    const int spmv_t = spmv_items(&t_eff);
+    long long ipt = (long long)kThreads * spmv_t;
+    if (!spmv) {
+        clamp_tile(&shape, dtype_size(vals_type));
+        if (L->merge_smem(shape) > kMaxSmem) return SPMM_ERR_INVALID_VALUE;
+        ipt = (long long)(merge_cta_threads(shape.W) / shape.W) * shape.ips;
+    }
+    const MergeLayout lay = merge_layout_items(m, nnz, n, ipt);
     bool own = false;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     if (!ws) {
@@ -491,10 +525,9 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     ma.use_tma = ((uintptr_t)row_ptr % 16 == 0) && ((uintptr_t)col_ind % 16 == 0) && ((uintptr_t)vals % 16 == 0);
     ma.wait_ns = kWaitLimitNs;
 
-    const int ipt = (merge_cta_threads(shape.W) / shape.W) * shape.ips;
-    st = spmm_merge_partition(m, nnz, row_ptr, ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
+    st = spmm_merge_partition(m, nnz, row_ptr, (int)ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
                               stream);
-    if (st == SPMM_OK) st = cuda_status(L->merge(ma, shape, sm_count(), s));
+    if (st == SPMM_OK) st = cuda_status(spmv ? L->spmv_merge(ma, spmv_t, s) : L->merge(ma, shape, sm_count(), s));
     if (st == SPMM_OK && lay.num_tiles > 1) st = cuda_status(L->fixup(ma, s));
     if (own) {
         const cudaError_t e = cudaFreeAsync(ws, s);
