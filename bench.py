@@ -60,10 +60,11 @@ def parse():
     p.add_argument("--ingest-ncu", default=None, metavar="CSV",
                    help="instead of the benchmark: turn the ncu CSV of the traffic capture (the command recorded in "
                         "profiles/merge_kernel_power_law_1M_dram.json, with --print-units base) into that JSON")
-    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv"],
+    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv", "tiling"],
                    help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
                         "n = 64), the density sweep against dense GEMM (100k x 100k, n = 64) or SpMV (n = 1) on "
-                        "five matrices against cuSPARSE through torch; JSON line per point")
+                        "five matrices against cuSPARSE through torch, or the A/B tiling against both families "
+                        "with B larger than L2; JSON line per point")
     return p.parse_args()
 
 
@@ -700,6 +701,31 @@ def run_sweep(args):
             torch.cuda.empty_cache()
     elif args.sweep == "spmv":
         run_spmv_sweep(pkg, torch, dev, flush, stream, reps)
+    elif args.sweep == "tiling":
+        # dense rows and a B beyond L2: where staging B panels in shared memory should pay most
+        for m, k, per_row, nn in ((10_000, 1_000_000, 50_000, 64), (20_000, 1_000_000, 10_000, 64),
+                                  (4_000, 2_000_000, 100_000, 64), (10_000, 1_000_000, 50_000, 128)):
+            a = gen.uniform_rows(m, k, per_row, gen.SEED_BASE + 90)
+            rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
+            del a
+            B = torch.randn(k, nn, device=dev, generator=torch.Generator(device=dev).manual_seed(91))
+            C = torch.empty(m, nn, device=dev)
+            nnz = m * per_row
+            ws = torch.empty(max(256, pkg.workspace_size(m, k, nn, nnz, "merge")), dtype=torch.uint8, device=dev)
+            row = {"sweep": "tiling", "m": m, "k": k, "per_row": per_row, "nnz": nnz, "n": nn,
+                   "b_bytes": k * nn * 4, "l2_bytes": torch.cuda.get_device_properties(dev).L2_cache_size,
+                   "tiled_reuse": pkg.spmm_tiled_reuse(m, k, nnz, nn, pkg.F32)}
+            ref = None
+            for alg in ("row_split", "merge", "tiled"):
+                t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=nnz, workspace=ws), flush, stream,
+                          3)
+                if ref is None:
+                    ref = C.clone()
+                row[alg] = {"ms": t, "gflops": 2.0 * nnz * nn / t / 1e6, "max_abs_diff_vs_row_split":
+                            float((C - ref).abs().max())}
+            print(json.dumps(row), flush=True)
+            del rp, ci, v, B, C, ws
+            torch.cuda.empty_cache()
     else:
         # fixed fraction of nonzeros per row of a 100k x 100k matrix vs dense GEMM (the paper's Fig. 7)
         mk = 100_000
@@ -717,6 +743,13 @@ def run_sweep(args):
             t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg="auto_gb300", out=C, nnz=per_row * mk, tuning=tun),
                       flush, stream, reps)
             row["spmm"] = {"ms": t, "gflops": 2.0 * per_row * mk * n / t / 1e6}
+            ref = C.clone()
+            for alg in ("row_split", "tiled"):
+                t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=per_row * mk, tuning=tun),
+                          flush, stream, reps)
+                row[alg] = {"ms": t, "gflops": 2.0 * per_row * mk * n / t / 1e6,
+                            "max_abs_diff_vs_spmm": float((C - ref).abs().max())}
+            row["tiled_reuse"] = pkg.spmm_tiled_reuse(mk, mk, per_row * mk, n, pkg.F32)
             dense = torch.zeros(mk, mk, device=dev)
             dense.view(-1)[(torch.repeat_interleave(torch.arange(mk, device=dev), per_row) * mk + ci.long())] = v
             for tf32 in (False, True):

@@ -46,9 +46,19 @@ typedef enum {
     SPMM_ALG_AUTO = 0,      /* Section 5.4 heuristic on the mean row length     */
     SPMM_ALG_ROW_SPLIT = 1, /* Section 4.1, Algorithm I                         */
     SPMM_ALG_MERGE = 2,     /* Section 4.2, Algorithm II (Algorithm 1)          */
-    SPMM_ALG_AUTO_GB300 = 3 /* mean row length recalibrated on GB300 plus a
+    SPMM_ALG_AUTO_GB300 = 3, /* mean row length recalibrated on GB300 plus a
                                longest-row guard against Type 1 imbalance
                                (Section 3.2); see spmm_select_alg_gb300      */
+    SPMM_ALG_TILED = 4       /* row blocks of A times k-panels of B held in
+                               shared memory: the tiling of A and B that
+                               Section 6 proposes for denser matrices.  Rows
+                               must list their columns in increasing order
+                               (an entry that goes backwards is skipped and
+                               reported as SPMM_ERR_BAD_CSR in d_status).
+                               Needs 16-byte access to B and C; otherwise
+                               the call runs the row split.  Measured slower
+                               than the row split on GB300 at every density
+                               tried; no selector picks it               */
 } spmm_alg_t;
 
 typedef enum {
@@ -115,6 +125,15 @@ int spmm_select_alg(int m, long long nnz, double threshold);
  * and SPMM_ALG_ROW_SPLIT otherwise.  m == 0 returns row split.
  */
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type);
+
+/*
+ * Expected reuse of one staged B row under SPMM_ALG_TILED: the rows of A per
+ * CTA block (2048 / lanes per row; lanes = the power of two covering n in
+ * 16-byte vectors) times the density nnz / (m * k), i.e. how many of the
+ * block's nonzeros share each B row the tiling stages once.  0 for empty
+ * shapes.  Pure host function.
+ */
+double spmm_tiled_reuse(int m, int k, long long nnz, int n, int b_type);
 
 /*
  * Longest row of A (max over i of row_ptr[i+1] - row_ptr[i]) computed on the

@@ -21,7 +21,7 @@ import ctypes
 import os
 import threading
 
-ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300 = 0, 1, 2, 3
+ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300, ALG_TILED = 0, 1, 2, 3, 4
 F32, BF16, F16 = 0, 1, 2
 SEMIRING_PLUS_TIMES, SEMIRING_MIN_PLUS, SEMIRING_MAX_PLUS, SEMIRING_MAX_TIMES = 0, 1, 2, 3
 SEMIRINGS = {"plus_times": SEMIRING_PLUS_TIMES, "min_plus": SEMIRING_MIN_PLUS, "max_plus": SEMIRING_MAX_PLUS,
@@ -31,7 +31,7 @@ ERR_INVALID_VALUE, ERR_ALLOC, ERR_LAUNCH, ERR_BAD_CSR, ERR_TIMEOUT, ERR_UNSUPPOR
 PAPER_THRESHOLD = 9.35  # Section 5.4
 
 _ALG_NAMES = {"auto": ALG_AUTO, "row_split": ALG_ROW_SPLIT, "rowsplit": ALG_ROW_SPLIT, "merge": ALG_MERGE,
-              "auto_gb300": ALG_AUTO_GB300}
+              "auto_gb300": ALG_AUTO_GB300, "tiled": ALG_TILED}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspmm_gb300.so")
 _lock = threading.Lock()
@@ -60,6 +60,7 @@ _SIGNATURES = {
     "spmm_launch_count": ([], _ll),
     "spmm_select_alg": ([_i, _ll, _d], _i),
     "spmm_select_alg_gb300": ([_i, _ll, _ll, _i, _i], _i),
+    "spmm_tiled_reuse": ([_i, _i, _ll, _i, _i], _d),
     "spmm_csr_max_row_length": ([_i, _vp, ctypes.POINTER(_ll), _vp], _i),
     "spmm_csr": ([_i, _i, _i, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _vp], _i),
     "spmm_csr_ex": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _sz, _vp, _vp], _i),
@@ -127,6 +128,10 @@ def spmm_select_alg(m: int, nnz: int, threshold: float = 0.0) -> int:
 
 def spmm_select_alg_gb300(m: int, nnz: int, max_row_len: int, n: int, b_type: int = F32) -> int:
     return load().spmm_select_alg_gb300(m, nnz, max_row_len, n, b_type)
+
+
+def spmm_tiled_reuse(m: int, k: int, nnz: int, n: int, b_type: int = F32) -> float:
+    return load().spmm_tiled_reuse(m, k, nnz, n, b_type)
 
 
 def spmm_csr_max_row_length(m, row_ptr, stream) -> tuple[int, int]:

@@ -218,6 +218,27 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned),
+// completed by cp_async_wait<N>() once at most N newer groups are pending.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// VEC elements of T from shared memory (16-byte aligned when VEC > 1).
+template <typename T, int VEC>
+__device__ __forceinline__ Raw<T, VEC> lds_raw(const T* p) {
+    Raw<T, VEC> r;
+    if constexpr (VEC == 1) r.v = *p;
+    else if constexpr (sizeof(T) == 4) r.v = *reinterpret_cast<const float4*>(p);
+    else r.v = *reinterpret_cast<const uint4*>(p);
+    return r;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }

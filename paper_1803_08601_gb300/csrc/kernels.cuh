@@ -737,4 +737,152 @@ __global__ void __launch_bounds__(kThreads) spmv_merge_kernel(MergeArgs a) {
     }
 }
 
+// ============================================================================ A/B tiling
+//
+// Tiling of both A and B for denser matrices, the direction Section 6 names
+// for rows with many nonzeros (after Greiner and Jacob): a CTA owns a block of
+// rows and walks B in panels of KT rows held in shared memory (two buffers,
+// filled by 16-byte asynchronous copies while the other is used).  Every
+// nonzero of the block whose column falls in the current panel reads its B row
+// from shared memory, so one staged row serves all of the block's nonzeros in
+// that column instead of costing each of them an L2 gather.
+//
+// Each row keeps a cursor that moves once through its columns, so rows must
+// list their columns in increasing order; an entry whose column lies below the
+// current panel is reported as SPMM_ERR_BAD_CSR and skipped (never read out of
+// range).  Lane groups of W lanes own kTiledRows rows each (the rows g, g + S,
+// ...); within a group the in-panel entries of a row are loaded one per lane
+// and broadcast by shuffles, as in the row split.
+struct TiledArgs {
+    int m, n, k;
+    const int* row_ptr;
+    const int* col_ind;
+    const void* vals;
+    const void* B;
+    long long ldb;
+    void* C;
+    long long ldc;
+    int* status;
+};
+
+constexpr int kTiledRows = 8;           // rows per lane group
+constexpr int kTiledPanel = 32 * 1024;  // bytes of one B panel in shared memory
+
+template <typename TV, typename TB, int VEC, int W>
+struct TiledShape {
+    static constexpr int S = kThreads / W;                       // lane groups per CTA
+    static constexpr int RB = S * kTiledRows;                    // rows per CTA
+    static constexpr int SW = W * VEC;                           // columns per slab
+    static constexpr int KT = kTiledPanel / (SW * (int)sizeof(TB));  // B rows per panel
+    static constexpr int CPR = SW * (int)sizeof(TB) / 16;        // 16-byte copies per B row
+};
+
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
+__global__ void __launch_bounds__(kThreads) tiled_kernel(TiledArgs a) {
+    using TS = TiledShape<TV, TB, VEC, W>;
+    constexpr int R = kTiledRows;
+    static_assert(VEC * sizeof(TB) == 16, "tiling stages 16-byte vectors");
+    extern __shared__ __align__(16) unsigned char smem[];
+    TB* const panel0 = reinterpret_cast<TB*>(smem);
+    TB* const panel1 = reinterpret_cast<TB*>(smem + kTiledPanel);
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (W - 1);
+    const int g = threadIdx.x / W;
+    const int gshift = lane & ~(W - 1);
+    const unsigned gmask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
+    const long long slab_col = (long long)blockIdx.y * TS::SW;
+    const long long col0 = slab_col + (long long)sl * VEC;
+    const bool col_ok = col0 < a.n;
+    const TB* __restrict__ B = static_cast<const TB*>(a.B);
+    const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
+    const int* __restrict__ col = a.col_ind;
+
+    int p[R], re[R], nc[R];
+    float nv[R];
+    float acc[R][VEC];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const long long row = (long long)blockIdx.x * TS::RB + g + i * TS::S;
+        p[i] = row < a.m ? __ldg(a.row_ptr + row) : 0;
+        re[i] = row < a.m ? __ldg(a.row_ptr + row + 1) : 0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[i][e] = SR::identity();
+    }
+    // the next entry of each row for this lane: (column, value), column INT_MAX past the row's end
+    auto fetch = [&](int i) {
+        const int q = p[i] + sl;
+        nc[i] = q < re[i] ? __ldg(col + q) : INT_MAX;
+        nv[i] = q < re[i] ? load_f(vals + q) : 0.0f;
+    };
+#pragma unroll
+    for (int i = 0; i < R; ++i) fetch(i);
+
+    const int panels = (a.k + TS::KT - 1) / TS::KT;
+    // this thread's 16-byte pieces of a panel: rows r0, r0 + RS, ..., column piece `part`
+    constexpr int RS = kThreads / TS::CPR;  // panel rows covered by one pass of the CTA
+    const int part = threadIdx.x % TS::CPR, r0 = threadIdx.x / TS::CPR;
+    const long long bc = slab_col + (long long)part * VEC;
+    auto stage = [&](int t, TB* dst) {
+        if (bc < a.n) {
+            const long long base = (long long)t * TS::KT;
+#pragma unroll 4
+            for (int r = r0; r < TS::KT; r += RS)
+                if (base + r < a.k) cp_async16(dst + r * TS::SW + part * VEC, B + (base + r) * a.ldb + bc);
+        }
+        cp_async_commit();
+    };
+    stage(0, panel0);
+    for (int t = 0; t < panels; ++t) {
+        TB* const cur = (t & 1) ? panel1 : panel0;
+        if (t + 1 < panels) stage(t + 1, (t & 1) ? panel0 : panel1);
+        else cp_async_commit();  // an empty group keeps the wait count uniform
+        cp_async_wait<1>();      // this thread's copies of panel t have landed ...
+        __syncthreads();         // ... and every thread's
+        const int k0 = t * TS::KT, kend = min(a.k, k0 + TS::KT);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            for (;;) {
+                // the row's in-panel entries are a prefix of the group's lanes (columns increase)
+                const bool in = nc[i] < kend;
+                const unsigned ball = (__ballot_sync(kFullMask, in) >> gshift) & gmask;
+                const int cnt = ball == gmask ? W : __ffs(~ball) - 1;
+                const int cmax = __reduce_max_sync(kFullMask, cnt);
+                // four entries per step: their shuffles and shared-memory reads are independent
+                for (int j = 0; j < cmax; j += 4) {
+                    int cj[4];
+                    float vj[4];
+                    Raw<TB, VEC> bj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        cj[u] = __shfl_sync(kFullMask, nc[i], j + u, W);
+                        vj[u] = __shfl_sync(kFullMask, nv[i], j + u, W);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool use = j + u < cnt && cj[u] >= k0 && col_ok;
+                        bj[u] = use ? lds_raw<TB, VEC>(cur + (cj[u] - k0) * TS::SW + sl * VEC) : zero_raw<TB, VEC>();
+                        if (j + u < cnt && cj[u] < k0 && sl == 0)
+                            report(a.status, SPMM_ERR_BAD_CSR);  // columns not increasing: entry skipped
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (j + u < cnt && cj[u] >= k0) accum_raw<SR, TB, VEC>(acc[i], vj[u], bj[u]);
+                }
+                p[i] += cnt;
+                if (cnt > 0) fetch(i);
+                if (!__any_sync(kFullMask, cnt == W)) break;
+            }
+        }
+        __syncthreads();  // panel t's buffer is refilled in the next iteration
+    }
+    cp_async_wait<0>();
+    if (col_ok) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const long long row = (long long)blockIdx.x * TS::RB + g + i * TS::S;
+            if (row < a.m) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc[i]);
+        }
+    }
+}
+
 }  // namespace spmm

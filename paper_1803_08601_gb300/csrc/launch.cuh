@@ -28,6 +28,7 @@ using MergeSmemFn = size_t (*)(const Shape&);
 using FixupFn = cudaError_t (*)(const MergeArgs&, cudaStream_t);
 using SpmvRowSplitFn = cudaError_t (*)(const RowSplitArgs&, int lanes, cudaStream_t);
 using SpmvMergeFn = cudaError_t (*)(const MergeArgs&, int items_per_thread, cudaStream_t);
+using TiledFn = cudaError_t (*)(const TiledArgs&, const Shape&, cudaStream_t);
 
 struct Launchers {
     RowSplitFn rowsplit;
@@ -36,6 +37,7 @@ struct Launchers {
     FixupFn fixup;
     SpmvRowSplitFn spmv_rowsplit;  // n = 1
     SpmvMergeFn spmv_merge;        // n = 1, tiles of kThreads * items_per_thread items (4, 8 or 16)
+    TiledFn tiled;                 // A/B tiling; 16-byte vectors only (shape.vec > 1)
 };
 
 // defined in inst_*.cu
@@ -219,6 +221,43 @@ cudaError_t spmv_merge_launch(const MergeArgs& a, int items_per_thread, cudaStre
     return e;
 }
 
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
+cudaError_t tiled_launch_one(const TiledArgs& a, const Shape& s, cudaStream_t st) {
+    using TS = TiledShape<TV, TB, VEC, W>;
+    auto kern = tiled_kernel<TV, TB, TC, VEC, W, SR>;
+    constexpr int smem = 2 * kTiledPanel;
+    static thread_local int configured_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != configured_dev) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured_dev = dev;
+    }
+    const long long gx = (a.m + TS::RB - 1) / TS::RB;
+    if (gx > 0x7fffffffLL || s.slabs > 65535) return cudaErrorInvalidConfiguration;
+    kern<<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+template <typename TV, typename TB, typename TC, typename SR>
+cudaError_t tiled_launch(const TiledArgs& a, const Shape& s, cudaStream_t st) {
+    constexpr int V = Elem<TB>::kVec;
+    if (s.vec != V) return cudaErrorInvalidValue;
+    switch (s.W) {
+        case 1: return tiled_launch_one<TV, TB, TC, V, 1, SR>(a, s, st);
+        case 2: return tiled_launch_one<TV, TB, TC, V, 2, SR>(a, s, st);
+        case 4: return tiled_launch_one<TV, TB, TC, V, 4, SR>(a, s, st);
+        case 8: return tiled_launch_one<TV, TB, TC, V, 8, SR>(a, s, st);
+        case 16: return tiled_launch_one<TV, TB, TC, V, 16, SR>(a, s, st);
+        case 32: return tiled_launch_one<TV, TB, TC, V, 32, SR>(a, s, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename TV, int VEC>
 size_t merge_smem_vec(const Shape& s) {
     switch (s.W) {
@@ -240,7 +279,8 @@ size_t merge_smem(const Shape& s) {
 template <typename TV, typename TB, typename TC, typename SR = PlusTimes>
 Launchers make_launchers() {
     return Launchers{&rowsplit_launch<TV, TB, TC, SR>, &merge_launch<TV, TB, TC, SR>, &merge_smem<TV, TB, TC>,
-                     &fixup_launch<TC, SR>, &spmv_rowsplit_launch<TV, TB, TC, SR>, &spmv_merge_launch<TV, TB, TC, SR>};
+                     &fixup_launch<TC, SR>, &spmv_rowsplit_launch<TV, TB, TC, SR>, &spmv_merge_launch<TV, TB, TC, SR>,
+                     &tiled_launch<TV, TB, TC, SR>};
 }
 
 }  // namespace spmm

@@ -293,7 +293,7 @@ int cuda_status(cudaError_t e) {
 int check_args(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
                const void* B, long long ldb, const void* C, long long ldc, int alg) {
     if (m < 0 || k < 0 || n < 0 || nnz < -1 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
-    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_AUTO_GB300) return SPMM_ERR_INVALID_VALUE;
+    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_TILED) return SPMM_ERR_INVALID_VALUE;
     if (m > 0 && n > 0) {
         if (!row_ptr || !C) return SPMM_ERR_INVALID_VALUE;
         if (ldc < n) return SPMM_ERR_INVALID_VALUE;
@@ -356,6 +356,14 @@ int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, in
     return SPMM_ALG_ROW_SPLIT;
 }
 
+double spmm_tiled_reuse(int m, int k, long long nnz, int n, int b_type) {
+    if (m <= 0 || k <= 0 || n <= 0 || nnz <= 0 || dtype_size(b_type) == 0) return 0.0;
+    const long long chunks = ((long long)n + 16 / dtype_size(b_type) - 1) / (16 / dtype_size(b_type));
+    const int W = pow2_ceil(chunks);  // at most 32: wider B takes column slabs
+    const double rows_per_block = (double)(kThreads / W) * kTiledRows;
+    return rows_per_block * (double)nnz / ((double)m * (double)k);
+}
+
 int spmm_csr_max_row_length(int m, const int* row_ptr, long long* max_row_len, void* stream) {
     if (m < 0 || !max_row_len || (m > 0 && !row_ptr)) return SPMM_ERR_INVALID_VALUE;
     *max_row_len = 0;
@@ -385,6 +393,7 @@ int spmm_csr_max_row_length(int m, const int* row_ptr, long long* max_row_len, v
 size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int b_type, const spmm_tuning_t* tuning) {
     if (m < 0 || k < 0 || n < 0 || nnz < 0 || dtype_size(b_type) == 0) return 0;
     if (alg == SPMM_ALG_AUTO_GB300) alg = SPMM_ALG_MERGE;  // the choice may need the longest row: size for merge
+    if (alg == SPMM_ALG_TILED) return 0;
     if (resolve_alg(alg, m, nnz, tuning) != SPMM_ALG_MERGE || m == 0 || n == 0) return 0;
     // the access width depends on pointer alignment and the default slab count on the device's L2,
     // neither known here: size for every combination
@@ -471,7 +480,11 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
     if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
     const bool spmv = n == 1;  // y = A x: the SpMV forms of both families
-    if (a == SPMM_ALG_ROW_SPLIT) {
+    if (a == SPMM_ALG_TILED && shape.vec > 1 && !spmv) {
+        TiledArgs ta{m, n, k, row_ptr, col_ind, vals, B, ldb, C, ldc, d_status};
+        return cuda_status(L->tiled(ta, shape, s));
+    }
+    if (a == SPMM_ALG_ROW_SPLIT || a == SPMM_ALG_TILED) {  // tiling without 16-byte access: row split
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
         if (spmv)
             return cuda_status(

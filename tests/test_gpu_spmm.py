@@ -244,3 +244,71 @@ def test_power_law_workload_full_size_sampled(gpu_lib, n):
         C = gpu_lib.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=a.nnz)
         torch.cuda.synchronize()
         check(C[torch.from_numpy(rows).cuda()].cpu().numpy(), a.row_ptr, a.col_ind, a.vals, B, rows=rows)
+
+
+@pytest.mark.parametrize("name", ["uniform16", "power_law", "short_rows", "alternating_empty", "empty_runs",
+                                  "all_empty", "giant_row", "single_row", "one_nonzero", "tall_k1", "identity",
+                                  "permutation"])
+@pytest.mark.parametrize("n", [8, 13, 64, 128, 300])
+def test_tiled_structures(gpu_lib, name, n):
+    """A/B tiling on every structure with increasing columns (n = 13 has no
+    16-byte path and runs the row split)."""
+    import torch
+
+    rp, ci, v, k = structure(name)
+    if name == "permutation":  # one entry per row: trivially increasing
+        pass
+    B = gen.normal_matrix(k, n, 11 + n)
+    C = run(gpu_lib, torch, rp, ci, v, B, "tiled")
+    check(C.cpu().numpy(), rp, ci, v, B)
+
+
+@pytest.mark.parametrize("n", [8, 32, 64, 128, 256])
+def test_tiled_integer_arithmetic_is_bitwise(gpu_lib, n):
+    """Integer data across many k-panels (k = 12,000 spans 23-188 panels): the
+    tiled sum must equal the oracle exactly."""
+    import torch
+
+    rng = np.random.default_rng(n + 1)
+    lens = rng.integers(0, 400, 3000)
+    lens[::97] = 8000
+    rp, ci, v = csr_arrays(lens, 12_000, 6, int_vals=True)
+    B = rng.integers(-4, 5, size=(12_000, n)).astype(np.float32)
+    C = run(gpu_lib, torch, rp, ci, v, B, "tiled").cpu().numpy()
+    assert np.array_equal(C, oracle.spmm(rp, ci, v, B).astype(np.float32))
+
+
+def test_tiled_reports_rows_that_go_backwards(gpu_lib):
+    """Columns must increase within a row: a row that goes backwards across a
+    panel boundary is reported (SPMM_ERR_BAD_CSR) and its late entry skipped;
+    every other row is still exact."""
+    import torch
+
+    k, n = 4000, 64
+    rp = np.array([0, 3, 5, 7], dtype=np.int32)
+    ci = np.array([5, 3000, 7, 10, 20, 1, 2], dtype=np.int32)  # row 0: 3000 then 7 (backwards)
+    v = np.ones(7, dtype=np.float32)
+    B = np.arange(k * n, dtype=np.float32).reshape(k, n) % 7
+    d_rp, d_ci, d_v, d_B = to_dev(torch, rp, ci, v, B)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = gpu_lib.spmm(d_rp, d_ci, d_v, d_B, alg="tiled", nnz=7, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == gpu_lib.ERR_BAD_CSR
+    C = C.cpu().numpy()
+    assert np.array_equal(C[0], B[5] + B[3000])  # the backwards entry (column 7) skipped
+    assert np.array_equal(C[1:], oracle.spmm(rp, ci, v, B).astype(np.float32)[1:])
+
+
+@pytest.mark.parametrize("combo", [("bf16", "bf16", "bf16"), ("bf16", "bf16", "f32"), ("f16", "f16", "f16"),
+                                   ("bf16", "f16", "f32")])
+def test_tiled_16bit(gpu_lib, combo):
+    from test_gpu_precision import OUT_TOL, errors, run_case
+
+    import torch
+
+    rp, ci, v, k = structure("uniform16")
+    B = gen.normal_matrix(k, 64, 62)
+    got, v_r, B_r = run_case(gpu_lib, torch, rp, ci, v, B, combo, "tiled")
+    e_r, e_o = errors(got, rp, ci, v, B, v_r, B_r, out=combo[2])
+    assert e_r <= OUT_TOL[combo[2]], e_r
+    assert e_o <= 1e-2, e_o

@@ -89,6 +89,8 @@ def test_argument_checks_return_before_any_device_work(lib):
     assert call(ldb=3) == pkg.ERR_INVALID_VALUE
     assert call(ldc=2) == pkg.ERR_INVALID_VALUE
     assert call(alg=7) == pkg.ERR_INVALID_VALUE
+    assert call(alg=5) == pkg.ERR_INVALID_VALUE
+    assert call(alg=pkg.ALG_TILED, m=0) == pkg.OK
     assert call(row_ptr=None) == pkg.ERR_INVALID_VALUE
     assert call(C=None) == pkg.ERR_INVALID_VALUE
     assert call(col_ind=None) == pkg.ERR_INVALID_VALUE
@@ -144,3 +146,13 @@ def test_no_cpu_path():
     t = torch.zeros(3, dtype=torch.int32)
     with pytest.raises(ValueError):
         pkg.spmm(t, t[:0], torch.zeros(0), torch.zeros(2, 2))
+
+
+def test_tiled_needs_no_workspace_and_reuse_formula(lib):
+    assert pkg.workspace_size(1000, 1000, 64, 16000, pkg.ALG_TILED) == 0
+    # 16 lanes per row at n = 64 float32: 256 / 16 groups x 8 rows = 128 rows per block
+    assert abs(pkg.spmm_tiled_reuse(100_000, 100_000, 500_000_000, 64, pkg.F32) - 128 * 0.05) < 1e-9
+    # 16-bit B: 8 elements per 16 bytes, n = 64 -> 8 lanes -> 256 rows per block
+    assert abs(pkg.spmm_tiled_reuse(1000, 1000, 1000, 64, pkg.BF16) - 256 * 1e-3) < 1e-12
+    assert pkg.spmm_tiled_reuse(0, 10, 0, 64, pkg.F32) == 0.0
+
