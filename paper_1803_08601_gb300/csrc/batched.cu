@@ -129,8 +129,18 @@ __global__ void batched_fixup_kernel(const MatDesc* __restrict__ mats, const int
     if (R < 0) return;
     const int b = tile_mat[i];
     if (i > 0 && tile_mat[i - 1] == b && carry_row_all[i - 1] == R) return;
+    // the run's last tile j, 32 tiles per probe (each warp of the block finds the same j)
+    const int lane = threadIdx.x & 31;
     int j = i;
-    while (j + 1 < total_tiles && tile_mat[j + 1] == b && carry_row_all[j + 1] == R) ++j;
+    for (int base = i + 1;; base += 32) {
+        const int t = base + lane;
+        const unsigned same =
+            __ballot_sync(kFullMask, t < total_tiles && tile_mat[t] == b && carry_row_all[t] == R);
+        if (same != kFullMask) {
+            j = base + __ffs(~same) - 2;
+            break;
+        }
+    }
     if (j + 1 >= total_tiles || tile_mat[j + 1] != b || head_row_all[j + 1] != R) {
         if (threadIdx.x == 0) report(status, SPMM_ERR_BAD_CSR);
         return;

@@ -539,14 +539,24 @@ __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int*
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < num_tiles; i += warps) {
         const int R = carry_row[i];
         if (R < 0 || (i > 0 && carry_row[i - 1] == R)) continue;
+        // the run's last tile j: the tiles carrying R are consecutive, so the
+        // first tile after i that does not carry R ends it (32 tiles per probe)
         int j = i;
-        while (j + 1 < num_tiles && carry_row[j + 1] == R) ++j;
+        for (int base = i + 1;; base += 32) {
+            const int t = base + lane;
+            const unsigned same = __ballot_sync(kFullMask, t < num_tiles && carry_row[t] == R);
+            if (same != kFullMask) {
+                j = base + __ffs(~same) - 2;
+                break;
+            }
+        }
         if (j + 1 >= num_tiles || head_row[j + 1] != R) {
             if (lane == 0) report(status, SPMM_ERR_BAD_CSR);
             continue;
         }
         for (int c = lane; c < n; c += 32) {
             float sum = SR::identity();
+#pragma unroll 8
             for (int t = i; t <= j; ++t) sum = SR::add(sum, carry[(size_t)t * n + c]);
             sum = SR::add(sum, head[(size_t)(j + 1) * n + c]);
             C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
