@@ -318,7 +318,8 @@ typedef enum {
 int spmm_batched_plan_create(int count, const spmm_batch_matrix_t *mats, int policy, void *stream,
                              spmm_batched_plan_t **plan);
 
-/* Enqueue the batch: the persistent kernel and the fix-up (two launches). */
+/* Enqueue the batch: a persistent kernel over the merge tiles, a persistent
+   kernel over the row-split chunks and the fix-up (up to three launches). */
 int spmm_batched_run(const spmm_batched_plan_t *plan, void *stream);
 
 /* Capture spmm_batched_run into a CUDA graph owned by the plan (replaces a

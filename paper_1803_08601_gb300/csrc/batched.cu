@@ -88,33 +88,42 @@ __device__ __forceinline__ void batched_tile(const MatDesc& d, int* carry_row_al
     __syncthreads();
 }
 
-// Three CTAs per SM: caps the registers of the (inlined) worst-case variant at 80.
+// Row-split items: a lean kernel of its own (no shared memory, the row
+// split's registers), so that it runs at the occupancy of the row split.
+__global__ void __launch_bounds__(kThreads)
+    batched_rows_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items) {
+    for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const Item item = items[it];
+        const MatDesc d = mats[item.mat];
+        const int slab = item.kind_slab >> 1;
+        switch (d.W) {
+            case 1: batched_rows<1>(d, item.a, item.b, slab); break;
+            case 2: batched_rows<2>(d, item.a, item.b, slab); break;
+            case 4: batched_rows<4>(d, item.a, item.b, slab); break;
+            case 8: batched_rows<8>(d, item.a, item.b, slab); break;
+            case 16: batched_rows<16>(d, item.a, item.b, slab); break;
+            default: batched_rows<32>(d, item.a, item.b, slab); break;
+        }
+    }
+}
+
+// Merge-tile items.  Three CTAs per SM: caps the registers of the (inlined)
+// worst-case tile variant at 80.
 __global__ void __launch_bounds__(kThreads, 3)
-    batched_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
-                   int* carry_row_all, int* head_row_all, int* status) {
+    batched_tiles_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
+                         int* carry_row_all, int* head_row_all, int* status) {
     extern __shared__ __align__(128) unsigned char smem[];
     for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
         const Item item = items[it];
         const MatDesc d = mats[item.mat];
         const int slab = item.kind_slab >> 1;
-        if ((item.kind_slab & 1) == 0) {
-            switch (d.W) {
-                case 1: batched_rows<1>(d, item.a, item.b, slab); break;
-                case 2: batched_rows<2>(d, item.a, item.b, slab); break;
-                case 4: batched_rows<4>(d, item.a, item.b, slab); break;
-                case 8: batched_rows<8>(d, item.a, item.b, slab); break;
-                case 16: batched_rows<16>(d, item.a, item.b, slab); break;
-                default: batched_rows<32>(d, item.a, item.b, slab); break;
-            }
-        } else {
-            switch (d.W) {
-                case 1: batched_tile<1>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-                case 2: batched_tile<2>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-                case 4: batched_tile<4>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-                case 8: batched_tile<8>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-                case 16: batched_tile<16>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-                default: batched_tile<32>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
-            }
+        switch (d.W) {
+            case 1: batched_tile<1>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
+            case 2: batched_tile<2>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
+            case 4: batched_tile<4>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
+            case 8: batched_tile<8>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
+            case 16: batched_tile<16>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
+            default: batched_tile<32>(d, carry_row_all, head_row_all, item.a, slab, smem, status); break;
         }
     }
 }
@@ -217,8 +226,10 @@ struct spmm_batched_plan {
     std::vector<int> ips;
     unsigned char* mem = nullptr;
     MatDesc* d_mats = nullptr;
-    Item* d_items = nullptr;
+    Item* d_items = nullptr;       // row-split items, then merge-tile items
     long long n_items = 0;
+    long long n_row_items = 0;
+    int grid_rows = 0;
     int total_tiles = 0;
     int* d_tile_mat = nullptr;
     int* d_carry_row = nullptr;
@@ -251,7 +262,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     p->mats = mats;
     cudaGetDevice(&p->device);
     std::vector<MatDesc> descs(mats.size());
-    std::vector<Item> items;
+    std::vector<Item> items, tile_items;
     std::vector<int> tile_mat;
     size_t carry_floats = 0, limit_entries = 0;
     size_t smem = 0;
@@ -282,7 +293,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
             const long long ipt = (long long)(kThreads / d.W) * d.ips;
             d.num_tiles = (int)((mt.m + mt.nnz + ipt - 1) / ipt);
             for (int sl = 0; sl < d.slabs; ++sl)
-                for (int t = 0; t < d.num_tiles; ++t) items.push_back(Item{(int)b, 1 | (sl << 1), t, 0});
+                for (int t = 0; t < d.num_tiles; ++t) tile_items.push_back(Item{(int)b, 1 | (sl << 1), t, 0});
             for (int t = 0; t < d.num_tiles; ++t) tile_mat.push_back((int)b);
             carry_floats += (size_t)d.num_tiles * mt.n;
             limit_entries += d.num_tiles + 1;
@@ -294,6 +305,8 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
                 for (int r = 0; r < mt.m; r += chunk) items.push_back(Item{(int)b, sl << 1, r, std::min(mt.m, r + chunk)});
         }
     }
+    p->n_row_items = (long long)items.size();
+    items.insert(items.end(), tile_items.begin(), tile_items.end());
     p->n_items = (long long)items.size();
     p->total_tiles = (int)tile_mat.size();
     // one device allocation: descriptors, items, tile map, row marks, limits, carries, heads, status
@@ -347,23 +360,36 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     if (st == SPMM_OK && e != cudaSuccess) st = status_of(e);
     p->smem = smem;
     if (st == SPMM_OK && smem > 48 * 1024)
-        st = status_of(cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int blocks = 0, sms = 0;
-    if (st == SPMM_OK) st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batched_kernel, kThreads, smem));
+        st = status_of(cudaFuncSetAttribute(batched_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = 0, blocks_rows = 0, sms = 0;
+    if (st == SPMM_OK)
+        st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batched_tiles_kernel, kThreads, smem));
+    if (st == SPMM_OK)
+        st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_rows, batched_rows_kernel, kThreads, 0));
     if (st == SPMM_OK) st = status_of(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     if (st != SPMM_OK) {
         destroy_plan(p);
         return st;
     }
-    p->grid = (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks, 1) * sms, p->n_items));
+    const long long n_tile_items = p->n_items - p->n_row_items;
+    p->grid = (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks, 1) * sms, n_tile_items));
+    p->grid_rows =
+        (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks_rows, 1) * sms, p->n_row_items));
     *out = p;
     return SPMM_OK;
 }
 
 int run_plan(const spmm_batched_plan* p, cudaStream_t s) {
-    if (p->n_items > 0) {
-        batched_kernel<<<p->grid, kThreads, p->smem, s>>>(p->d_mats, p->d_items, p->n_items, p->d_carry_row,
-                                                         p->d_head_row, p->d_status);
+    const long long n_tile_items = p->n_items - p->n_row_items;
+    if (n_tile_items > 0) {
+        batched_tiles_kernel<<<p->grid, kThreads, p->smem, s>>>(p->d_mats, p->d_items + p->n_row_items, n_tile_items,
+                                                               p->d_carry_row, p->d_head_row, p->d_status);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (p->n_row_items > 0) {
+        batched_rows_kernel<<<p->grid_rows, kThreads, 0, s>>>(p->d_mats, p->d_items, p->n_row_items);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return status_of(e);
         g_launches.fetch_add(1, std::memory_order_relaxed);

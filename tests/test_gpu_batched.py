@@ -1,4 +1,4 @@
-"""GPU parity of the batched form (one persistent launch over many CSR
+"""GPU parity of the batched form (persistent launches over many CSR
 products of uneven sizes, graph replay, autotuned schedule) with the oracle."""
 import numpy as np
 import pytest
@@ -55,7 +55,7 @@ def test_batched_policies(gpu_lib, policy):
     c0 = pkg.spmm_launch_count()
     plan.run()
     torch.cuda.synchronize()
-    assert pkg.spmm_launch_count() - c0 <= 2
+    assert pkg.spmm_launch_count() - c0 <= 3  # merge tiles, row chunks, fix-up: independent of the batch size
     check_all(host, dev)
     # graph replay, with new values of B between replays
     plan.capture_graph()
