@@ -524,8 +524,42 @@ def e2e(pkg, torch, a, ns, Bs, args, tuning):
             pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning)
     t = (time.perf_counter() - t0) / reps
     flops = sum(2.0 * a.nnz * n for n in ns)
+    link = host_link(torch)
+    bound_ms = (h2d + d2h) / (link["duplex_gbs"] * 1e9) * 1e3
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3, "api": "spmm_csr_host"}
+            "ms_per_step": t * 1e3, "api": "spmm_csr_host", "link": link,
+            "link_bound_ms": bound_ms, "frac_of_link_bound": bound_ms / (t * 1e3)}
+
+
+def host_link(torch, nbytes=256 << 20, reps=5):
+    """Pinned host <-> device copy bandwidth (GB/s): one direction at a time and both at once.
+    The e2e step cannot beat (h2d + d2h bytes) / duplex bandwidth."""
+    dev = torch.device("cuda")
+    n = nbytes // 4
+    h_up, h_down = torch.empty(n).pin_memory(), torch.empty(n).pin_memory()
+    d_up, d_down = torch.empty(n, device=dev), torch.empty(n, device=dev)
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def rate(fn, moved):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return moved * reps / (time.perf_counter() - t0) / 1e9
+
+    def duplex():
+        with torch.cuda.stream(s_up):
+            d_up.copy_(h_up, non_blocking=True)
+        with torch.cuda.stream(s_down):
+            h_down.copy_(d_down, non_blocking=True)
+
+    out = {"h2d_gbs": rate(lambda: d_up.copy_(h_up, non_blocking=True), nbytes),
+           "d2h_gbs": rate(lambda: h_down.copy_(d_down, non_blocking=True), nbytes),
+           "duplex_gbs": rate(duplex, 2 * nbytes), "copy_bytes": nbytes}
+    del h_up, h_down, d_up, d_down
+    return out
 
 
 
