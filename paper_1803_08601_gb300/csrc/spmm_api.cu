@@ -14,10 +14,6 @@ namespace spmm {
 
 std::atomic<long long> g_launches{0};
 
-int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind,
-             const void* vals, int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type,
-             long long ldc, int alg, const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes,
-             int* d_status, void* stream);
 
 // Merge-path tiles (Section 4.2): the path that merges the row end offsets
 // row_ptr[1..m] with the nonzero indices 0..nnz-1 is cut into tiles of equal
@@ -315,6 +311,106 @@ int read_nnz(const int* row_ptr, int m, cudaStream_t st, long long* nnz) {
 }
 
 }  // namespace
+
+// The body of every C = A (x) B entry point (spmm_csr_ex, spmm_csr_semiring):
+// argument checks, algorithm choice, launch shape, then row split, SpMV, A/B
+// tiling or partition + merge + fix-up with the given launcher table.
+int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind,
+             const void* vals, int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type,
+             long long ldc, int alg, const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes,
+             int* d_status, void* stream) {
+    int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
+    if (st != SPMM_OK) return st;
+    if (!L) return SPMM_ERR_UNSUPPORTED;
+    if (m == 0 || n == 0) return SPMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nnz < 0) {
+        st = read_nnz(row_ptr, m, s, &nnz);
+        if (st != SPMM_OK) return st;
+    }
+    Shape shape;
+    if (alg == SPMM_ALG_AUTO_GB300) {
+        long long lmax = tuning ? tuning->max_row_len : 0;
+        if (lmax <= 0) {
+            st = spmm_csr_max_row_length(m, row_ptr, &lmax, stream);
+            if (st != SPMM_OK) return st;
+        }
+        alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
+    }
+    const int a = resolve_alg(alg, m, nnz, tuning);
+    spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
+    if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
+    if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
+    const bool spmv = n == 1;  // y = A x: the SpMV forms of both families
+    if (a == SPMM_ALG_TILED && shape.vec > 1 && !spmv) {
+        TiledArgs ta{m, n, k, row_ptr, col_ind, vals, B, ldb, C, ldc, d_status};
+        return cuda_status(L->tiled(ta, shape, s));
+    }
+    if (a == SPMM_ALG_ROW_SPLIT || a == SPMM_ALG_TILED) {  // tiling without 16-byte access: row split
+        RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
+        if (spmv)
+            return cuda_status(
+                L->spmv_rowsplit(ra, t_eff.lanes_per_row > 0 ? t_eff.lanes_per_row : spmv_lanes(m, nnz), s));
+        return cuda_status(L->rowsplit(ra, shape, s));
+    }
+
+    // merge based: partition, compute, fix-up.  SpMM tiles are capped so that
+    // the double-buffered staging fits the shared memory of one CTA.
+    const int spmv_t = spmv_items(&t_eff);
+    long long ipt = (long long)kThreads * spmv_t;
+    if (!spmv) {
+        clamp_tile(&shape, dtype_size(vals_type));
+        if (L->merge_smem(shape) > kMaxSmem) return SPMM_ERR_INVALID_VALUE;
+        ipt = (long long)(merge_cta_threads(shape.W) / shape.W) * shape.ips;
+    }
+    const MergeLayout lay = merge_layout_items(m, nnz, n, ipt);
+    bool own = false;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    if (!ws) {
+        if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
+        void* p = nullptr;
+        keep_pool_memory();
+        const cudaError_t e = cudaMallocAsync(&p, lay.total, s);
+        if (e != cudaSuccess) return SPMM_ERR_ALLOC;
+        ws = static_cast<unsigned char*>(p);
+        own = true;
+    } else if (workspace_bytes < lay.total || ((uintptr_t)ws % 256) != 0) {
+        return SPMM_ERR_WORKSPACE;
+    }
+    MergeArgs ma{};
+    ma.m = m;
+    ma.n = n;
+    ma.nnz = nnz;
+    ma.row_ptr = row_ptr;
+    ma.col_ind = col_ind;
+    ma.vals = vals;
+    ma.B = B;
+    ma.ldb = ldb;
+    ma.C = C;
+    ma.ldc = ldc;
+    ma.limits = reinterpret_cast<const int2*>(ws + lay.off_limits);
+    ma.num_tiles = lay.num_tiles;
+    ma.slabs = shape.slabs;
+    ma.ips = shape.ips;
+    ma.carry = reinterpret_cast<float*>(ws + lay.off_carry);
+    ma.head = reinterpret_cast<float*>(ws + lay.off_head);
+    ma.carry_row = reinterpret_cast<int*>(ws + lay.off_carry_row);
+    ma.head_row = reinterpret_cast<int*>(ws + lay.off_head_row);
+    ma.status = d_status;
+    ma.use_tma = ((uintptr_t)row_ptr % 16 == 0) && ((uintptr_t)col_ind % 16 == 0) && ((uintptr_t)vals % 16 == 0);
+    ma.wait_ns = kWaitLimitNs;
+
+    st = spmm_merge_partition(m, nnz, row_ptr, (int)ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
+                              stream);
+    if (st == SPMM_OK) st = cuda_status(spmv ? L->spmv_merge(ma, spmv_t, s) : L->merge(ma, shape, sm_count(), s));
+    if (st == SPMM_OK && lay.num_tiles > 1) st = cuda_status(L->fixup(ma, s));
+    if (own) {
+        const cudaError_t e = cudaFreeAsync(ws, s);
+        if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    }
+    return st;
+}
+
 }  // namespace spmm
 
 using namespace spmm;
@@ -449,109 +545,6 @@ int spmm_csr_semiring(int m, int k, int n, long long nnz, const int* row_ptr, co
                           tuning, workspace, workspace_bytes, d_status, stream);
 }
 
-}  // extern "C"
-
-namespace spmm {
-
-int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind,
-             const void* vals, int vals_type, const void* B, int b_type, long long ldb, void* C, int c_type,
-             long long ldc, int alg, const spmm_tuning_t* tuning, void* workspace, size_t workspace_bytes,
-             int* d_status, void* stream) {
-    int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
-    if (st != SPMM_OK) return st;
-    if (!L) return SPMM_ERR_UNSUPPORTED;
-    if (m == 0 || n == 0) return SPMM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (nnz < 0) {
-        st = read_nnz(row_ptr, m, s, &nnz);
-        if (st != SPMM_OK) return st;
-    }
-    Shape shape;
-    if (alg == SPMM_ALG_AUTO_GB300) {
-        long long lmax = tuning ? tuning->max_row_len : 0;
-        if (lmax <= 0) {
-            st = spmm_csr_max_row_length(m, row_ptr, &lmax, stream);
-            if (st != SPMM_OK) return st;
-        }
-        alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
-    }
-    const int a = resolve_alg(alg, m, nnz, tuning);
-    spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
-    if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
-    if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
-    const bool spmv = n == 1;  // y = A x: the SpMV forms of both families
-    if (a == SPMM_ALG_TILED && shape.vec > 1 && !spmv) {
-        TiledArgs ta{m, n, k, row_ptr, col_ind, vals, B, ldb, C, ldc, d_status};
-        return cuda_status(L->tiled(ta, shape, s));
-    }
-    if (a == SPMM_ALG_ROW_SPLIT || a == SPMM_ALG_TILED) {  // tiling without 16-byte access: row split
-        RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
-        if (spmv)
-            return cuda_status(
-                L->spmv_rowsplit(ra, t_eff.lanes_per_row > 0 ? t_eff.lanes_per_row : spmv_lanes(m, nnz), s));
-        return cuda_status(L->rowsplit(ra, shape, s));
-    }
-
-    // merge based: partition, compute, fix-up.  SpMM tiles are capped so that
-    // the double-buffered staging fits the shared memory of one CTA.
-    const int spmv_t = spmv_items(&t_eff);
-    long long ipt = (long long)kThreads * spmv_t;
-    if (!spmv) {
-        clamp_tile(&shape, dtype_size(vals_type));
-        if (L->merge_smem(shape) > kMaxSmem) return SPMM_ERR_INVALID_VALUE;
-        ipt = (long long)(merge_cta_threads(shape.W) / shape.W) * shape.ips;
-    }
-    const MergeLayout lay = merge_layout_items(m, nnz, n, ipt);
-    bool own = false;
-    unsigned char* ws = static_cast<unsigned char*>(workspace);
-    if (!ws) {
-        if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
-        void* p = nullptr;
-        keep_pool_memory();
-        const cudaError_t e = cudaMallocAsync(&p, lay.total, s);
-        if (e != cudaSuccess) return SPMM_ERR_ALLOC;
-        ws = static_cast<unsigned char*>(p);
-        own = true;
-    } else if (workspace_bytes < lay.total || ((uintptr_t)ws % 256) != 0) {
-        return SPMM_ERR_WORKSPACE;
-    }
-    MergeArgs ma{};
-    ma.m = m;
-    ma.n = n;
-    ma.nnz = nnz;
-    ma.row_ptr = row_ptr;
-    ma.col_ind = col_ind;
-    ma.vals = vals;
-    ma.B = B;
-    ma.ldb = ldb;
-    ma.C = C;
-    ma.ldc = ldc;
-    ma.limits = reinterpret_cast<const int2*>(ws + lay.off_limits);
-    ma.num_tiles = lay.num_tiles;
-    ma.slabs = shape.slabs;
-    ma.ips = shape.ips;
-    ma.carry = reinterpret_cast<float*>(ws + lay.off_carry);
-    ma.head = reinterpret_cast<float*>(ws + lay.off_head);
-    ma.carry_row = reinterpret_cast<int*>(ws + lay.off_carry_row);
-    ma.head_row = reinterpret_cast<int*>(ws + lay.off_head_row);
-    ma.status = d_status;
-    ma.use_tma = ((uintptr_t)row_ptr % 16 == 0) && ((uintptr_t)col_ind % 16 == 0) && ((uintptr_t)vals % 16 == 0);
-    ma.wait_ns = kWaitLimitNs;
-
-    st = spmm_merge_partition(m, nnz, row_ptr, (int)ipt, lay.num_tiles, reinterpret_cast<int*>(ws + lay.off_limits),
-                              stream);
-    if (st == SPMM_OK) st = cuda_status(spmv ? L->spmv_merge(ma, spmv_t, s) : L->merge(ma, shape, sm_count(), s));
-    if (st == SPMM_OK && lay.num_tiles > 1) st = cuda_status(L->fixup(ma, s));
-    if (own) {
-        const cudaError_t e = cudaFreeAsync(ws, s);
-        if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
-    }
-    return st;
-}
-
-}  // namespace spmm
-
-extern "C" {
 
 int spmm_csr(int m, int k, int n, const int* row_ptr, const int* col_ind, const float* vals, const float* B,
              long long ldb, float* C, long long ldc, int alg, void* stream) {
