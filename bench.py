@@ -60,11 +60,12 @@ def parse():
     p.add_argument("--ingest-ncu", default=None, metavar="CSV",
                    help="instead of the benchmark: turn the ncu CSV of the traffic capture (the command recorded in "
                         "profiles/merge_kernel_power_law_1M_dram.json, with --print-units base) into that JSON")
-    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv", "tiling"],
+    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv", "tiling", "selector"],
                    help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
                         "n = 64), the density sweep against dense GEMM (100k x 100k, n = 64) or SpMV (n = 1) on "
-                        "five matrices against cuSPARSE through torch, or the A/B tiling against both families "
-                        "with B larger than L2; JSON line per point")
+                        "five matrices against cuSPARSE through torch, the A/B tiling against both families "
+                        "with B larger than L2, or both selectors over row-length families (selector); "
+                        "JSON line per point")
     return p.parse_args()
 
 
@@ -735,6 +736,8 @@ def run_sweep(args):
             torch.cuda.empty_cache()
     elif args.sweep == "spmv":
         run_spmv_sweep(pkg, torch, dev, flush, stream, reps)
+    elif args.sweep == "selector":
+        run_selector_sweep(pkg, torch, dev, flush, stream, reps)
     elif args.sweep == "tiling":
         # dense rows and a B beyond L2: where staging B panels in shared memory should pay most
         for m, k, per_row, nn in ((10_000, 1_000_000, 50_000, 64), (20_000, 1_000_000, 10_000, 64),
@@ -795,6 +798,50 @@ def run_sweep(args):
             del rp, ci, v, C, dense
             torch.cuda.empty_cache()
     return 0
+
+
+def run_selector_sweep(pkg, torch, dev, flush, stream, reps):
+    """Both families on 1M x 1M matrices of three row-length families (every row the same length,
+    Poisson lengths, power-law lengths with density exponent 2 capped at 10^5) and mean lengths
+    2-64, at n = 8, 32, 64, 128; each point records the two times, the Section 5.4 rule's pick,
+    the GB300 selector's pick and each pick's time relative to the faster family (1 = right)."""
+    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    m = k = 1_000_000
+    Bs = {n: torch.randn(k, n, device=dev, generator=torch.Generator(device=dev).manual_seed(300 + n))
+          for n in (8, 32, 64, 128)}
+    rng = np.random.default_rng(gen.SEED_BASE + 95)
+    families = {"uniform": (2, 4, 6, 8, 12, 16, 32, 64), "poisson": (2, 4, 6, 8, 12, 16, 32, 64),
+                "power_law": (12, 16, 32, 64)}  # exponent 2 with minimum 1 and the cap keeps the mean >= ~12
+    for family, means in families.items():
+        for d in means:
+            if family == "uniform":
+                lens = np.full(m, d, dtype=np.int64)
+            elif family == "poisson":
+                lens = rng.poisson(d, m).astype(np.int64)
+            else:
+                lens, _ = gen.power_law_lengths(m, k, gen.SEED_BASE + 96 + d, mean=float(d))
+            a = gen.csr_from_lengths(np.minimum(lens, k), k, gen.SEED_BASE + 97 + d)
+            rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
+            nnz, lmax = a.nnz, int(np.diff(a.row_ptr).max()) if m else 0
+            del a
+            for n, B in Bs.items():
+                C = torch.empty(m, n, device=dev)
+                ws = torch.empty(max(256, pkg.workspace_size(m, k, n, nnz, "merge")), dtype=torch.uint8, device=dev)
+                t = {}
+                for alg in ("row_split", "merge"):
+                    r = 1 if (alg == "row_split" and lmax > 20_000) else reps
+                    t[alg] = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=nnz, workspace=ws), flush,
+                                   stream, r)
+                best = min(t.values())
+                paper = name[pkg.spmm_select_alg(m, nnz, 0.0)]
+                gb300 = name[pkg.spmm_select_alg_gb300(m, nnz, lmax, n, pkg.F32)]
+                print(json.dumps({"sweep": "selector", "family": family, "mean_row": nnz / m, "max_row": lmax,
+                                  "n": n, "nnz": nnz, "row_split_ms": t["row_split"], "merge_ms": t["merge"],
+                                  "paper_pick": paper, "paper_regret": t[paper] / best,
+                                  "gb300_pick": gb300, "gb300_regret": t[gb300] / best}), flush=True)
+                del C, ws
+            del rp, ci, v
+            torch.cuda.empty_cache()
 
 
 def run_spmv_sweep(pkg, torch, dev, flush, stream, reps):

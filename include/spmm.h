@@ -119,9 +119,12 @@ int spmm_select_alg(int m, long long nnz, double threshold);
  *     (Type 1 imbalance, Section 3.2): max_row_len > 1024 and
  *     max_row_len * 8192 > nnz (fitted on a GB300 sweep of dense-as-CSR
  *     matrices from 2 x 2^23 to 2^23 x 2), or
- *   - the mean row length nnz / m is below 5 and a row of B is at least 64
- *     bytes (n * element size of B); measured crossover of the two kernels on
- *     GB300 for uniform rows (the paper's 9.35 was measured on a K40c);
+ *   - a row of B is at least 64 bytes (n * element size of B) and the mean
+ *     row length d = nnz / m is below a threshold T: T = 7 for rows of B of
+ *     256 bytes or more, T = 3 for 64-255 bytes, and 2T when the longest row is
+ *     at least 2d (uneven rows); measured crossovers of the two kernels on
+ *     GB300 for uniform and Poisson row lengths (the paper's single 9.35 was
+ *     measured on a K40c);
  * and SPMM_ALG_ROW_SPLIT otherwise.  m == 0 returns row split.
  */
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type);

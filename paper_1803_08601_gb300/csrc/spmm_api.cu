@@ -448,8 +448,13 @@ int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, in
     if (max_row_len > 1024 && max_row_len * 8192 > nnz) return SPMM_ALG_MERGE;  // Type 1 guard
     const double d = (double)nnz / (double)m;
     const long long row_bytes = (long long)n * (dtype_size(b_type) ? dtype_size(b_type) : 4);
-    if (row_bytes >= 64 && d < 5.0) return SPMM_ALG_MERGE;
-    return SPMM_ALG_ROW_SPLIT;
+    if (row_bytes < 64) return SPMM_ALG_ROW_SPLIT;
+    // mean-length crossover measured on GB300 (uniform and Poisson rows, 1M x 1M): about 7 nonzeros
+    // per row for rows of B of 256 bytes or more, 3 below; about twice that when the longest row is
+    // at least twice the mean (uneven rows cost the row split more than the merge path)
+    double threshold = row_bytes >= 256 ? 7.0 : 3.0;
+    if ((double)max_row_len >= 2.0 * d) threshold *= 2.0;
+    return d < threshold ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT;
 }
 
 double spmm_tiled_reuse(int m, int k, long long nnz, int n, int b_type) {

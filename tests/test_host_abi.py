@@ -61,11 +61,22 @@ def test_gb300_selector(lib):
     # the aspect-ratio sweep's boundary: 4096 rows of 4096 go to merge, 8192 rows of 2048 to row split
     assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 64, F) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg_gb300(8192, 1 << 24, 2048, 64, F) == pkg.ALG_ROW_SPLIT
-    # recalibrated mean-length rule: short rows go to merge only with rows of B of >= 64 bytes
-    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 64, F) == pkg.ALG_MERGE
-    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 8, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(10**6, 3 * 10**6, 3, 32, H) == pkg.ALG_MERGE
-    assert pkg.spmm_select_alg_gb300(10**6, 6 * 10**6, 6, 64, F) == pkg.ALG_ROW_SPLIT
+    # mean-length rule (points of the row-length family sweep, 1M x 1M): never merge below 64-byte
+    # rows of B; threshold 7 for rows of 256 bytes or more, 3 for 64-255 bytes; doubled for uneven rows
+    M = 10**6
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 8, F) == pkg.ALG_ROW_SPLIT        # 32-byte rows
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 32, F) == pkg.ALG_MERGE           # uniform, 128 B
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 4, 32, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 32, H) == pkg.ALG_MERGE           # 64-byte bf16 rows
+    assert pkg.spmm_select_alg_gb300(M, 6 * M, 6, 64, F) == pkg.ALG_MERGE           # uniform, 256 B
+    assert pkg.spmm_select_alg_gb300(M, 8 * M, 8, 64, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 6 * M, 6, 128, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(M, 8 * M, 8, 128, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 16, 32, F) == pkg.ALG_MERGE          # Poisson-like, 128 B
+    assert pkg.spmm_select_alg_gb300(M, 8 * M, 24, 32, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 12 * M, 33, 64, F) == pkg.ALG_MERGE         # Poisson-like, 256 B
+    assert pkg.spmm_select_alg_gb300(M, 16 * M, 40, 64, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 32 * M, 61, 128, F) == pkg.ALG_ROW_SPLIT    # longest < 2 x mean
     assert pkg.spmm_select_alg_gb300(0, 0, 0, 64, F) == pkg.ALG_ROW_SPLIT
 
 
