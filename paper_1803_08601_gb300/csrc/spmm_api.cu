@@ -244,7 +244,7 @@ void clamp_tile(Shape* s, int sv) {
 
 // Stream-ordered allocations of this library come from the device's default
 // memory pool.  Its default release threshold (0) hands freed memory back to
-// the driver at every synchronisation, which makes each call pay the full
+// the CUDA driver at every synchronisation, which makes each call pay the full
 // mapping cost again; keep it cached instead (once per device, for this
 // process only).
 void keep_pool_memory() {
