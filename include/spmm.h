@@ -13,14 +13,19 @@
  *     rows + nonzeros into equal tiles, a compute pass per tile, and a
  *     carry-out fix-up for rows that cross tiles;
  *   - the Section 5.4 heuristic: merge based when nnz / m < 9.35.
+ * Beyond the paper: a GB300-calibrated selector, SpMV kernels of both
+ * families for n = 1, 16-bit storage forms, semiring products, an A/B-tiled
+ * kernel, the backward pass (transpose, SDDMM), batched plans and a
+ * host-buffer entry point.
  *
  * Conventions shared by every entry point unless stated otherwise:
  *   - Array arguments are DEVICE pointers owned by the caller; the library
  *     keeps no reference after the call returns.
  *   - Indices are 0-based int32.  row_ptr has m + 1 entries, row_ptr[0] = 0,
  *     non-decreasing; 0 <= col_ind[p] < k.  Column indices inside a row need
- *     not be sorted; repeated indices are summed.  Out-of-range indices are a
- *     precondition violation (not checked; the result is undefined).
+ *     not be sorted (except for SPMM_ALG_TILED); repeated indices are summed.
+ *     Out-of-range indices are a precondition violation (not checked; the
+ *     result is undefined).
  *   - Dense matrices are row-major with leading dimension (row stride, in
  *     elements) ldb >= n, ldc >= n.
  *   - C is overwritten (beta = 0); rows of A without nonzeros give zero rows.
@@ -29,8 +34,10 @@
  *   - `stream` is a cudaStream_t handle (NULL = the legacy default stream).
  *     Work is enqueued asynchronously; a return of SPMM_OK means the launch
  *     was accepted, not that the kernels finished.  Errors found on the
- *     device (bounded waits that ran out) are written to the optional device
- *     status word `d_status` as SPMM_ERR_TIMEOUT.
+ *     device are written to the optional device status word `d_status`:
+ *     SPMM_ERR_TIMEOUT for a bounded wait that ran out, SPMM_ERR_BAD_CSR for
+ *     an inconsistent fix-up run or (SPMM_ALG_TILED) a row whose columns go
+ *     backwards.  The first error stays; the caller clears the word.
  *   - No entry point aborts, throws, or falls back to the CPU.
  */
 #ifndef SPMM_GB300_H
@@ -164,8 +171,12 @@ int spmm_csr(int m, int k, int n, const int *row_ptr, const int *col_ind, const 
  * (bf16,f16,f32), (f16,f16,f16) and (f16,f16,f32); others return
  * SPMM_ERR_UNSUPPORTED.  `tuning` may be NULL.
  * workspace: device memory of at least spmm_csr_workspace_size(...) bytes for
- * the merge-based algorithm (row split needs none); NULL with
- * workspace_bytes == 0 makes the call allocate it stream-ordered itself.
+ * the merge-based algorithm (row split and SPMM_ALG_TILED need none); NULL
+ * with workspace_bytes == 0 makes the call allocate it stream-ordered itself.
+ * n == 1 (y = A x) runs the SpMV kernels of the chosen family: the row split
+ * with tuning->lanes_per_row lanes per row (0: from the mean row length) and
+ * the merge based with 4, 8 or 16 path items per thread
+ * (tuning->items_per_subwarp; 0: 8).
  * The workspace must not be used by another call that may run concurrently.
  * d_status: optional device int; a bounded wait that runs out stores
  * SPMM_ERR_TIMEOUT there (the caller clears it).
