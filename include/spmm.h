@@ -233,9 +233,13 @@ int spmm_merge_partition(int m, long long nnz, const int *row_ptr, int items_per
 /*
  * C = A B with every array in HOST memory: the call copies A and B to the
  * device, computes, copies C back and synchronises `stream` before it returns.
- * Types and alg as in spmm_csr_ex; nnz is read from the host row_ptr[m].
- * Device buffers are obtained stream-ordered and released before return.
- * Pinned (page-locked) host buffers make the copies asynchronous DMA.
+ * Types and alg as in spmm_csr_ex; nnz is read from the host row_ptr[m]
+ * (SPMM_ALG_AUTO_GB300 without tuning->max_row_len scans the host row_ptr for
+ * the longest row).  Copies and compute are pipelined: B and C in column
+ * slabs, A in up to four row chunks, so that the first block is computed as
+ * soon as its pieces are on the device.  Device buffers are obtained
+ * stream-ordered and released before return.  Pinned (page-locked) host
+ * buffers make the copies asynchronous DMA.
  */
 int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
                   int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,

@@ -117,6 +117,12 @@ int resolve_alg(int alg, int m, long long nnz, const spmm_tuning_t* t) {
     return spmm_select_alg(m, nnz, threshold_of(t));
 }
 
+// row_ptr[i] -= base for i < count: a row chunk's offsets made to start at 0.
+__global__ void rebase_kernel(int* __restrict__ row_ptr, int count, int base) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) row_ptr[i] -= base;
+}
+
 // Longest row by a grid-stride max reduction over row_ptr differences.
 __global__ void row_length_max_kernel(const int* __restrict__ row_ptr, int m, int* __restrict__ out) {
     int best = 0;
@@ -572,66 +578,131 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
     keep_pool_memory();
     cudaStream_t up = nullptr, down = nullptr;
     if (!copy_streams(&up, &down)) return SPMM_ERR_CUDA;
-    // Device copies: B and C packed with leading dimension n (rounded to 16 bytes for the vector path).
+
+    // The algorithm is chosen once, for the whole matrix.
+    spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
+    if (alg == SPMM_ALG_AUTO_GB300) {
+        if (t.max_row_len <= 0)
+            for (int i = 0; i < m; ++i) t.max_row_len = std::max<long long>(t.max_row_len, row_ptr[i + 1] - row_ptr[i]);
+        alg = spmm_select_alg_gb300(m, nnz, t.max_row_len, n, b_type);
+    }
+    alg = resolve_alg(alg, m, nnz, &t);
+
+    // Pipeline over the full-duplex host link.  Column slabs of B and C (at least 128 bytes of a
+    // row each) let slab j be computed while slab j+1 of B goes up and slab j-1 of C comes down;
+    // row chunks of A (equal shares of rows + nonzeros) let the first slab start as soon as the
+    // first chunk of A is on the device instead of all of A.  Order on the upload stream:
+    // B slab 0, A chunk 0 .. R-1, B slab 1 .. S-1.
     const long long vb = 16 / sb, vc = 16 / sc;
     const long long ldb_d = (n + vb - 1) / vb * vb, ldc_d = (n + vc - 1) / vc * vc;
-    const size_t b_rp = align256((size_t)(m + 1) * 4), b_col = align256((size_t)nnz * 4),
-                 b_val = align256((size_t)nnz * sv), b_B = align256((size_t)k * ldb_d * sb),
-                 b_C = align256((size_t)m * ldc_d * sc);
-    // Column slabs pipeline the full-duplex host link: while slab j is computed, slab j+1 of B
-    // is uploaded and slab j-1 of C downloaded.  A slab is at least 128 bytes of a row.
     int slabs = (int)std::min<long long>(4, std::max<long long>(1, (long long)n * sb / 128));
     long long w = (n + slabs - 1) / slabs;
     w = (w + 15) / 16 * 16;  // whole 16-byte vectors for every element size
     slabs = (int)((n + w - 1) / w);
+    const long long a_bytes = (long long)(m + 1) * 4 + nnz * (4 + sv);
+    const int chunks = (int)std::max<long long>(1, std::min<long long>({4, m, a_bytes / (8LL << 20)}));
+    std::vector<int> r(chunks + 1);  // chunk c holds rows [r[c], r[c+1])
+    r[0] = 0;
+    r[chunks] = m;
+    for (int c = 1; c < chunks; ++c) {  // equal shares of the merge path (rows + nonzeros)
+        const long long target = ((long long)m + nnz) * c / chunks;
+        int lo = r[c - 1], hi = m;
+        while (lo < hi) {
+            const int mid = lo + (hi - lo) / 2;
+            if ((long long)mid + row_ptr[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        r[c] = lo;
+    }
+    // Each chunk's row_ptr (rebased to 0), col_ind and vals start on a 256-byte boundary, so the
+    // merge kernel keeps its bulk-copy staging.
+    std::vector<size_t> off_rp(chunks), off_col(chunks), off_val(chunks);
+    size_t total = 0;
+    for (int c = 0; c < chunks; ++c) {
+        const long long cnnz = row_ptr[r[c + 1]] - row_ptr[r[c]];
+        off_rp[c] = total;
+        total += align256((size_t)(r[c + 1] - r[c] + 1) * 4);
+        off_col[c] = total;
+        total += align256((size_t)cnnz * 4);
+        off_val[c] = total;
+        total += align256((size_t)cnnz * sv);
+    }
+    const size_t off_B = total, off_C = off_B + align256((size_t)k * ldb_d * sb);
+    total = off_C + align256((size_t)m * ldc_d * sc);
     void* mem = nullptr;
-    cudaError_t e = cudaMallocAsync(&mem, b_rp + b_col + b_val + b_B + b_C, s);
+    cudaError_t e = cudaMallocAsync(&mem, total, s);
     if (e != cudaSuccess) return SPMM_ERR_ALLOC;
     unsigned char* base = static_cast<unsigned char*>(mem);
-    int* d_rp = reinterpret_cast<int*>(base);
-    int* d_col = reinterpret_cast<int*>(base + b_rp);
-    void* d_val = base + b_rp + b_col;
-    unsigned char* d_B = base + b_rp + b_col + b_val;
-    unsigned char* d_C = base + b_rp + b_col + b_val + b_B;
-    std::vector<cudaEvent_t> ev(2 + 2 * (size_t)slabs, nullptr);
+    unsigned char* d_B = base + off_B;
+    unsigned char* d_C = base + off_C;
+    std::vector<cudaEvent_t> ev(1 + chunks + slabs + (size_t)slabs * chunks, nullptr);
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-    cudaEvent_t e_alloc = ev[0], e_a = ev[1];
-    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_alloc, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, row_ptr, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, up);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col_ind, (size_t)nnz * 4, cudaMemcpyHostToDevice, up);
-    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, vals, (size_t)nnz * sv, cudaMemcpyHostToDevice, up);
-    if (e == cudaSuccess) e = cudaEventRecord(e_a, up);
-    for (int j = 0; j < slabs && e == cudaSuccess; ++j) {
+    cudaEvent_t e_alloc = ev[0];
+    cudaEvent_t* e_a = ev.data() + 1;                // chunk c of A uploaded
+    cudaEvent_t* e_b = ev.data() + 1 + chunks;       // slab j of B uploaded
+    cudaEvent_t* e_c = ev.data() + 1 + chunks + slabs;  // block (j, c) of C computed
+    auto upload_b = [&](int j) {
         const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
+        cudaError_t x = cudaSuccess;
         if (k > 0 && nnz > 0)
-            e = (slabs == 1 && ldb == ldb_d)
+            x = (slabs == 1 && ldb == ldb_d)
                     ? cudaMemcpyAsync(d_B, B, (size_t)k * ldb_d * sb, cudaMemcpyHostToDevice, up)
                     : cudaMemcpy2DAsync(d_B + c0 * sb, (size_t)ldb_d * sb, static_cast<const unsigned char*>(B) + c0 * sb,
                                         (size_t)ldb * sb, (size_t)cw * sb, (size_t)k, cudaMemcpyHostToDevice, up);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + j], up);
+        if (x == cudaSuccess) x = cudaEventRecord(e_b[j], up);
+        return x;
+    };
+    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_alloc, 0);
+    if (e == cudaSuccess) e = upload_b(0);
+    for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        const long long p0 = row_ptr[r[c]], p1 = row_ptr[r[c + 1]];
+        e = cudaMemcpyAsync(base + off_rp[c], row_ptr + r[c], (size_t)(r[c + 1] - r[c] + 1) * 4, cudaMemcpyHostToDevice,
+                            up);
+        if (e == cudaSuccess && p1 > p0)
+            e = cudaMemcpyAsync(base + off_col[c], col_ind + p0, (size_t)(p1 - p0) * 4, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess && p1 > p0)
+            e = cudaMemcpyAsync(base + off_val[c], static_cast<const unsigned char*>(vals) + p0 * sv,
+                                (size_t)(p1 - p0) * sv, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess) e = cudaEventRecord(e_a[c], up);
     }
+    for (int j = 1; j < slabs && e == cudaSuccess; ++j) e = upload_b(j);
     if (e != cudaSuccess) st = cuda_status(e);
-    // the selector's inputs are computed once for all slabs
-    spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
-    if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(s, e_a, 0));
-    if (st == SPMM_OK && alg == SPMM_ALG_AUTO_GB300 && t.max_row_len <= 0)
-        st = spmm_csr_max_row_length(m, d_rp, &t.max_row_len, stream);
+
     for (int j = 0; j < slabs && st == SPMM_OK; ++j) {
         const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
-        st = cuda_status(cudaStreamWaitEvent(s, ev[2 + j], 0));
-        if (st == SPMM_OK)
-            st = spmm_csr_ex(m, k, (int)cw, nnz, d_rp, d_col, d_val, vals_type, d_B + c0 * sb, b_type, ldb_d,
-                             d_C + c0 * sc, c_type, ldc_d, alg, &t, nullptr, 0, nullptr, stream);
-        if (st == SPMM_OK) st = cuda_status(cudaEventRecord(ev[2 + slabs + j], s));
-        if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, ev[2 + slabs + j], 0));
-        if (st == SPMM_OK)
-            st = cuda_status((slabs == 1 && ldc == ldc_d)
-                                 ? cudaMemcpyAsync(C, d_C, (size_t)m * ldc_d * sc, cudaMemcpyDeviceToHost, down)
-                                 : cudaMemcpy2DAsync(static_cast<unsigned char*>(C) + c0 * sc, (size_t)ldc * sc,
-                                                     d_C + c0 * sc, (size_t)ldc_d * sc, (size_t)cw * sc, (size_t)m,
-                                                     cudaMemcpyDeviceToHost, down));
+        st = cuda_status(cudaStreamWaitEvent(s, e_b[j], 0));
+        for (int c = 0; c < chunks && st == SPMM_OK; ++c) {
+            const int rows = r[c + 1] - r[c];
+            const long long p0 = row_ptr[r[c]], cnnz = row_ptr[r[c + 1]] - p0;
+            int* rp_c = reinterpret_cast<int*>(base + off_rp[c]);
+            if (j == 0) {  // chunk c arrives once: rebase its row offsets to start at 0
+                st = cuda_status(cudaStreamWaitEvent(s, e_a[c], 0));
+                if (st == SPMM_OK && p0 != 0) {
+                    rebase_kernel<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(rp_c, rows + 1, (int)p0);
+                    const cudaError_t x = cudaGetLastError();
+                    if (x == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+                    st = cuda_status(x);
+                }
+            }
+            if (st == SPMM_OK && rows > 0)
+                st = spmm_csr_ex(rows, k, (int)cw, cnnz, rp_c, reinterpret_cast<const int*>(base + off_col[c]),
+                                 base + off_val[c], vals_type, d_B + c0 * sb,
+                                 b_type, ldb_d, d_C + ((size_t)r[c] * ldc_d + c0) * sc, c_type, ldc_d, alg, &t, nullptr,
+                                 0, nullptr, stream);
+            cudaEvent_t done = e_c[(size_t)j * chunks + c];
+            if (st == SPMM_OK) st = cuda_status(cudaEventRecord(done, s));
+            if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, done, 0));
+            if (st == SPMM_OK && rows > 0) {
+                unsigned char* hc = static_cast<unsigned char*>(C) + ((size_t)r[c] * ldc + c0) * sc;
+                const unsigned char* dc = d_C + ((size_t)r[c] * ldc_d + c0) * sc;
+                st = cuda_status((slabs == 1 && ldc == ldc_d)
+                                     ? cudaMemcpyAsync(hc, dc, (size_t)rows * ldc_d * sc, cudaMemcpyDeviceToHost, down)
+                                     : cudaMemcpy2DAsync(hc, (size_t)ldc * sc, dc, (size_t)ldc_d * sc, (size_t)cw * sc,
+                                                         (size_t)rows, cudaMemcpyDeviceToHost, down));
+            }
+        }
     }
     // release after every stream that touched the buffer is done with it
     cudaStreamSynchronize(up);

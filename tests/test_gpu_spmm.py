@@ -312,3 +312,38 @@ def test_tiled_16bit(gpu_lib, combo):
     e_r, e_o = errors(got, rp, ci, v, B, v_r, B_r, out=combo[2])
     assert e_r <= OUT_TOL[combo[2]], e_r
     assert e_o <= 1e-2, e_o
+
+
+@pytest.mark.parametrize("n", [8, 64, 128])
+def test_host_entry_row_chunks(gpu_lib, n):
+    """spmm_csr_host splits A into up to four row chunks of at least 8 MB (equal shares of rows +
+    nonzeros, each uploaded, rebased and computed on its own): runs of empty rows, a row of
+    300,000 nonzeros and short rows, checked on every row against the oracle."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(n)
+    lens = rng.integers(0, 48, 200_000)
+    lens[50_000:60_000] = 0
+    lens[123_456] = 300_000
+    lens[-5000:] = 0
+    rp, ci, v = csr_arrays(lens, 400_000, 12)
+    assert len(rp) * 4 + 8 * int(rp[-1]) >= 32 << 20  # A's bytes: four chunks of at least 8 MB
+    B = gen.normal_matrix(400_000, n, 13)
+    for alg in ALGS:
+        C = torch.full((len(rp) - 1, n), float("nan")).pin_memory()
+        pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), torch.from_numpy(B), C, alg=alg)
+        check(C.numpy(), rp, ci, v, B)
+
+
+def test_host_entry_few_long_rows(gpu_lib):
+    """Three rows of two million nonzeros: at most as many chunks as rows."""
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v = csr_arrays(np.array([2_000_000, 0, 2_000_000, 2_000_000]), 2_500_000, 14)
+    B = gen.normal_matrix(2_500_000, 16, 15)
+    for alg in ("row_split", "merge", "auto_gb300"):
+        C = torch.empty((4, 16)).pin_memory()
+        pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), torch.from_numpy(B), C, alg=alg)
+        check(C.numpy(), rp, ci, v, B)
