@@ -56,3 +56,19 @@ def test_noalloc_rejects_problems_beyond_its_scratch(gpu_lib):
     st = pkg.spmm_csr_noalloc(m, m, n, nnz, 256, 512, 768, pkg.F32, 1024, pkg.F32, n, 2048, pkg.F32, n,
                               pkg.ALG_MERGE, None, None, None)
     assert st == pkg.ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("alg,n", [("merge", 1), ("row_split", 1), ("tiled", 64)])
+def test_noalloc_spmv_and_tiled_match_bitwise(gpu_lib, alg, n):
+    """The SpMV merge kernel keeps its tiles' carries in the same fixed scratch (tiles of 2048
+    path items), and the A/B tiling needs none; both give the regular entry point's bits."""
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("giant_row" if alg != "tiled" else "uniform16")
+    B = gen.normal_matrix(k, n, 60 + n)
+    d_rp, d_ci, d_v, d_B = (torch.from_numpy(x).cuda() for x in (rp, ci, v, B))
+    C_new = _noalloc(pkg, torch, d_rp, d_ci, d_v, d_B, int(rp[-1]), alg)
+    C_ref = pkg.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=int(rp[-1]))
+    torch.cuda.synchronize()
+    assert torch.equal(C_new, C_ref)
