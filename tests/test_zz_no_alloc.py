@@ -58,17 +58,27 @@ def test_noalloc_rejects_problems_beyond_its_scratch(gpu_lib):
     assert st == pkg.ERR_WORKSPACE
 
 
-@pytest.mark.parametrize("alg,n", [("merge", 1), ("row_split", 1), ("tiled", 64)])
-def test_noalloc_spmv_and_tiled_match_bitwise(gpu_lib, alg, n):
+@pytest.mark.parametrize("alg", ["merge", "row_split"])
+def test_noalloc_spmv_matches_bitwise(gpu_lib, alg):
     """The SpMV merge kernel keeps its tiles' carries in the same fixed scratch (tiles of 2048
-    path items), and the A/B tiling needs none; both give the regular entry point's bits."""
+    path items); both SpMV kernels give the regular entry point's bits."""
     import torch
 
     pkg = gpu_lib
-    rp, ci, v, k = structure("giant_row" if alg != "tiled" else "uniform16")
-    B = gen.normal_matrix(k, n, 60 + n)
+    rp, ci, v, k = structure("giant_row")
+    B = gen.normal_matrix(k, 1, 61)
     d_rp, d_ci, d_v, d_B = (torch.from_numpy(x).cuda() for x in (rp, ci, v, B))
     C_new = _noalloc(pkg, torch, d_rp, d_ci, d_v, d_B, int(rp[-1]), alg)
     C_ref = pkg.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=int(rp[-1]))
     torch.cuda.synchronize()
     assert torch.equal(C_new, C_ref)
+
+
+def test_noalloc_accepts_only_its_documented_algorithms():
+    """AUTO, ROW_SPLIT and MERGE only: AUTO_GB300 would allocate to measure the longest row, and
+    the A/B tiling is not offered here; both are rejected before any device work."""
+    import paper_1803_08601_gb300 as pkg
+
+    for alg in (pkg.ALG_AUTO_GB300, pkg.ALG_TILED):
+        st = pkg.spmm_csr_noalloc(4, 4, 4, 4, 8, 16, 32, pkg.F32, 64, pkg.F32, 4, 128, pkg.F32, 4, alg, None, None, None)
+        assert st == pkg.ERR_INVALID_VALUE
