@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kThreads) tiled_kernel(TiledArgs a) {
     using TS = TiledShape<TV, TB, VEC, W>;
     constexpr int R = kTiledRows;
     static_assert(VEC * sizeof(TB) == 16, "tiling stages 16-byte vectors");
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     TB* const panel0 = reinterpret_cast<TB*>(smem);
     TB* const panel1 = reinterpret_cast<TB*>(smem + kTiledPanel);
     const int lane = threadIdx.x & 31;

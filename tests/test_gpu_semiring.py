@@ -43,7 +43,7 @@ def expect_exact(C, rp, ci, v, B, semiring):
 @pytest.mark.parametrize("name", STRUCTURES)
 @pytest.mark.parametrize("alg", ["row_split", "merge"])
 @pytest.mark.parametrize("semiring", SEMIRINGS)
-@pytest.mark.parametrize("n", [1, 13, 128])
+@pytest.mark.parametrize("n", [1, 8, 13, 128])
 def test_structures_bitwise(gpu_lib, name, alg, semiring, n):
     import torch
 
