@@ -271,6 +271,100 @@ __global__ void __launch_bounds__(kThreads) sddmm_kernel(SddmmArgs a) {
     }
 }
 
+// Wide rows (n >= 32 16-byte vectors, up to 256): a warp per run of `chunk`
+// consecutive nonzeros.  Its first row comes from a 32-ary warp search of
+// row_ptr; the current row of dC stays in registers (lane l holds vectors
+// l, l + 32, ...) and is reloaded only when the row changes; up to U nonzeros
+// of one row are done together, their rows of B gathered with independent
+// loads (U * CPL vectors in flight per lane), and each dot product is reduced
+// across the warp with xor shuffles in the same order as sddmm_kernel.
+template <typename TD, typename TO, int CPL, int U>
+__global__ void __launch_bounds__(kThreads) sddmm_warp_kernel(SddmmArgs a) {
+    constexpr int VEC = Elem<TD>::kVec;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long p0 = wid * a.chunk;
+    if (p0 >= a.nnz) return;  // whole warps leave together
+    const long long p1 = p0 + a.chunk < a.nnz ? p0 + a.chunk : a.nnz;
+    const TD* __restrict__ dC = static_cast<const TD*>(a.dC);
+    const TD* __restrict__ B = static_cast<const TD*>(a.B);
+    const int nchunks = a.n / VEC;
+    // first row: the largest r with row_ptr[r] <= p0 (row_ptr[0] = 0 <= p0 always holds)
+    int lo = 0, hi = a.m;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        const long long span = hi - lo;
+        const int x = lo + (int)((span * lane) / 32);
+        const unsigned ball = __ballot_sync(kFullMask, (long long)__ldg(a.row_ptr + x) <= p0);
+        const int cnt = __popc(ball);  // a prefix of the lanes, at least lane 0
+        const int x_last = lo + (int)((span * (cnt - 1)) / 32);
+        hi = cnt < 32 ? lo + (int)((span * cnt) / 32) : hi;
+        lo = x_last;
+    }
+    int row = lo;
+    int row_end = __ldg(a.row_ptr + row + 1);
+    float y[CPL][VEC];
+    auto load_row = [&]() {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int j = lane + 32 * c;
+            if (j < nchunks) load_vec<TD, VEC>(dC + (long long)row * a.lddc + (long long)j * VEC, y[c]);
+            else
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) y[c][e] = 0.0f;
+        }
+    };
+    load_row();
+    for (long long p = p0; p < p1;) {
+        if (p >= row_end) {  // warp-uniform: the next nonzero belongs to a later row
+            do {
+                ++row;
+                row_end = __ldg(a.row_ptr + row + 1);
+            } while (p >= row_end);
+            load_row();
+        }
+        const long long pe = p1 < (long long)row_end ? p1 : (long long)row_end;
+        const int cnt = pe - p < U ? (int)(pe - p) : U;
+        int cols[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cols[u] = u < cnt ? __ldg(a.col_ind + p + u) : 0;
+        Raw<TD, VEC> x[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int j = lane + 32 * c;
+                x[u][c] = (u < cnt && j < nchunks) ? load_raw<TD, VEC>(B + (long long)cols[u] * a.ldb + (long long)j * VEC)
+                                                   : zero_raw<TD, VEC>();
+            }
+        float part[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            part[u] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                float t[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) t[e] = 0.0f;
+                fma_raw<TD, VEC>(t, 1.0f, x[u][c]);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) part[u] = fmaf(t[e], y[c][e], part[u]);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(kFullMask, part[u], off);
+        if (lane < cnt) {
+            float mine = part[0];
+#pragma unroll
+            for (int u = 1; u < U; ++u)
+                if (lane == u) mine = part[u];
+            static_cast<TO*>(a.out)[p + lane] = Elem<TO>::from_f(mine);
+        }
+        p += cnt;
+    }
+}
+
 template <typename TD, typename TO, int VEC>
 cudaError_t sddmm_launch_vec(const SddmmArgs& a, int W, long long groups, cudaStream_t st) {
     const long long blocks = (groups * W + kThreads - 1) / kThreads;
@@ -296,6 +390,18 @@ int sddmm_run(const SddmmArgs& a0, cudaStream_t st) {
     const long long nchunks = ((long long)a.n + vec - 1) / vec;
     int W = 1;
     while (W < nchunks && W < 32) W <<= 1;
+    if (vec_ok && nchunks >= 32 && nchunks <= 256) {  // a warp per 256 nonzeros, dC rows in registers
+        a.chunk = 256;
+        const long long warps = (a.nnz + a.chunk - 1) / a.chunk;
+        const long long blocks = (warps * 32 + kThreads - 1) / kThreads;
+        if (blocks > 0x7fffffffLL) return SPMM_ERR_LAUNCH;
+        const int cpl = (int)((nchunks + 31) / 32);
+        if (cpl <= 1) sddmm_warp_kernel<TD, TO, 1, 8><<<(unsigned)blocks, kThreads, 0, st>>>(a);
+        else if (cpl <= 2) sddmm_warp_kernel<TD, TO, 2, 4><<<(unsigned)blocks, kThreads, 0, st>>>(a);
+        else if (cpl <= 4) sddmm_warp_kernel<TD, TO, 4, 2><<<(unsigned)blocks, kThreads, 0, st>>>(a);
+        else sddmm_warp_kernel<TD, TO, 8, 1><<<(unsigned)blocks, kThreads, 0, st>>>(a);
+        return launched(cudaGetLastError());
+    }
     a.chunk = 32;
     const long long groups = (a.nnz + a.chunk - 1) / a.chunk;
     const cudaError_t e = vec_ok ? sddmm_launch_vec<TD, TO, V>(a, W, groups, st) : sddmm_launch_vec<TD, TO, 1>(a, W, groups, st);

@@ -53,7 +53,7 @@ def test_transpose_large_column_count(gpu_lib):
 
 
 @pytest.mark.parametrize("name", ["power_law", "giant_row", "duplicates_unsorted", "short_rows", "tall_k1"])
-@pytest.mark.parametrize("n", [1, 8, 13, 64, 256])
+@pytest.mark.parametrize("n", [1, 8, 13, 64, 128, 256, 300, 1024])
 def test_sddmm(gpu_lib, name, n):
     import torch
 
@@ -69,12 +69,14 @@ def test_sddmm(gpu_lib, name, n):
     assert oracle.normalized_error(out.cpu().numpy(), ref, D) <= FP32_TOL
 
 
+@pytest.mark.parametrize("n", [64, 256, 1024])
 @pytest.mark.parametrize("dt,out_f32", [("bf16", False), ("bf16", True), ("f16", False), ("f16", True)])
-def test_sddmm_16bit(gpu_lib, dt, out_f32):
+def test_sddmm_16bit(gpu_lib, dt, out_f32, n):
+    """n = 64 takes the lane-group kernel; 256 and 1024 the warp kernel with dC rows in registers."""
     import torch
 
     rp, ci, v, k = structure("power_law")
-    m, n = len(rp) - 1, 64
+    m = len(rp) - 1
     dC = gen.normal_matrix(m, n, 31)
     B = gen.normal_matrix(k, n, 32)
     tdt = torch.bfloat16 if dt == "bf16" else torch.float16
