@@ -646,10 +646,21 @@ def form_backward(pkg, torch, flush, stream, steps, args):
                                  pkg.spmm(rpt, cit, vt, dY, alg="auto_gb300", out=dX, nnz=nnz,
                                           tuning={"max_row_len": lmax_t})), flush, stream, steps)
     t_sd = _time(torch, lambda: pkg.sddmm(rp, ci, dY, dX_in, out=dv), flush, stream, steps)
+    # the transpose on its own (a pattern that changes every step would pay it every step): outputs and
+    # workspace preallocated, device time
+    rpt2, cit2, perm2 = torch.empty_like(rpt), torch.empty_like(cit), torch.empty_like(perm)
+    ws_t = torch.empty(pkg.spmm_csr_transpose_workspace_size(a.m, a.k, nnz), dtype=torch.uint8, device=dev)
+    t_tr = _time(torch, lambda: pkg._check(pkg.spmm_csr_transpose(
+        a.m, a.k, nnz, rp.data_ptr(), ci.data_ptr(), rpt2.data_ptr(), cit2.data_ptr(), perm2.data_ptr(), ws_t.data_ptr(),
+        ws_t.numel(), stream.cuda_stream), "spmm_csr_transpose"), flush, stream, steps)
+    assert torch.equal(rpt2, rpt) and torch.equal(cit2, cit) and torch.equal(perm2, perm)
     # the plain float32 kernel on the forward shape, fixed family (reference point of the form)
     t_plain = _time(torch, lambda: A.spmm(v, dX_in, out=Y, alg=pkg.ALG_ROW_SPLIT), flush, stream, steps)
     return {"workload": "Chung-Lu GCN 500k, n=256", "nnz": nnz, "mean_degree": a.info["mean_degree"],
-            "max_degree": a.info["max_degree"], "transpose_once_ms": t_transpose,
+            "max_degree": a.info["max_degree"], "transpose_first_call_ms": t_transpose,
+            "transpose": {"ms": t_tr, "note": "stable radix sort by column, device time with preallocated "
+                                               "outputs; the first call above also allocates and measures the "
+                                               "longest row of A^T"},
             "forward": {"ms": t_fwd, "gflops": flops / t_fwd / 1e6},
             "dX_AT_dY": {"ms": t_dx, "gflops": flops / t_dx / 1e6, "includes": "vals gather + SpMM on A^T"},
             "dvals_sddmm": {"ms": t_sd, "gflops": flops / t_sd / 1e6},

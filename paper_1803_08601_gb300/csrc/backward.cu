@@ -51,7 +51,7 @@ int radix_passes(int k) {
 
 struct TransposeLayout {
     int tiles;
-    size_t off_k0, off_k1, off_v, off_hist, total;
+    size_t off_k0, off_k1, off_v, off_hist, off_tot, total;
 };
 
 TransposeLayout transpose_layout(long long nnz) {
@@ -66,6 +66,8 @@ TransposeLayout transpose_layout(long long nnz) {
     off = a256(off + (size_t)nnz * 4);
     L.off_hist = off;
     off = a256(off + (size_t)kRadix * (L.tiles > 0 ? L.tiles : 1) * 4);
+    L.off_tot = off;
+    off = a256(off + (size_t)kRadix * 4);
     L.total = off;
     return L;
 }
@@ -85,29 +87,64 @@ __global__ void radix_hist_kernel(const int* __restrict__ keys, long long n, int
     hist[(long long)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// In-place exclusive prefix sum of data[0..len) by one CTA: each thread sums a
-// contiguous chunk, the chunk sums are scanned in shared memory, then each
-// thread rewrites its chunk.  Only used on radix histograms (256 x tiles).
-__global__ void exclusive_scan_kernel(int* __restrict__ data, long long len) {
-    __shared__ long long part[kScanThreads];
-    const long long per = (len + kScanThreads - 1) / kScanThreads;
-    const long long lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
-    long long s = 0;
-    for (long long i = lo; i < hi; ++i) s += data[i];
-    part[threadIdx.x] = s;
+// Exclusive prefix sums of the digit-major histogram [256][tiles]: one CTA per
+// digit scans its row in place (chunks of kScanThreads coalesced elements,
+// warp shuffles, a running carry) and leaves the row's total in totals[d];
+// digit_base_kernel then turns the 256 totals into the digits' first
+// positions, which the scatter adds to each row's prefix.
+__global__ void digit_scan_kernel(int* __restrict__ hist, int tiles, int* __restrict__ totals) {
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int warp_sum[kWarps];
+    __shared__ int carry;
+    int* row = hist + (long long)blockIdx.x * tiles;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
     __syncthreads();
-    for (int off = 1; off < kScanThreads; off <<= 1) {  // Hillis-Steele inclusive scan
-        const long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    for (int base = 0; base < tiles; base += kScanThreads) {
+        const int i = base + tid;
+        const int v = i < tiles ? row[i] : 0;
+        int x = v;  // inclusive scan inside the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFullMask, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {  // inclusive scan of the warp sums
+            int w = warp_sum[lane];
+#pragma unroll
+            for (int off = 1; off < kWarps; off <<= 1) {
+                const int y = __shfl_up_sync(kFullMask, w, off);
+                if (lane >= off) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        if (i < tiles) row[i] = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
+        __syncthreads();
+        if (tid == 0) carry += warp_sum[kWarps - 1];
         __syncthreads();
     }
-    long long run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-    for (long long i = lo; i < hi; ++i) {
-        const int v = data[i];
-        data[i] = (int)run;
-        run += v;
+    if (tid == 0) totals[blockIdx.x] = carry;
+}
+
+// totals[d] <- sum of totals[0..d): the first sorted position of digit d (one CTA of 256 threads).
+__global__ void digit_base_kernel(int* __restrict__ totals) {
+    __shared__ int warp_sum[kRadix / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int v = totals[tid];
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, x, off);
+        if (lane >= off) x += y;
     }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    totals[tid] = before + x - v;
 }
 
 // Stable scatter of one radix pass.  A tile is consumed in rounds of 256
@@ -117,13 +154,14 @@ __global__ void exclusive_scan_kernel(int* __restrict__ data, long long len) {
 // per-digit base.  Element order is therefore kept among equal digits.
 // payload_in == nullptr means the payload is the element's own index.
 __global__ void radix_scatter_kernel(const int* __restrict__ keys_in, const int* __restrict__ payload_in, long long n,
-                                     int shift, int tiles, const int* __restrict__ offsets, int* __restrict__ keys_out,
+                                     int shift, int tiles, const int* __restrict__ offsets,
+                                     const int* __restrict__ digit_base, int* __restrict__ keys_out,
                                      int* __restrict__ payload_out) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ int base[kRadix];
     __shared__ int wcnt[kWarps][kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    base[tid] = offsets[(long long)tid * tiles + blockIdx.x];
+    base[tid] = offsets[(long long)tid * tiles + blockIdx.x] + digit_base[tid];
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
     __syncthreads();
@@ -170,19 +208,13 @@ __global__ void transpose_rowptr_kernel(const int* __restrict__ sorted_keys, lon
     row_ptr_t[c] = (int)lo;
 }
 
-// col_ind_t[q] = row of A holding nonzero perm[q] (last row whose start <= perm[q]).
-__global__ void transpose_rows_kernel(const int* __restrict__ row_ptr, int m, const int* __restrict__ perm,
-                                      long long nnz, int* __restrict__ col_ind_t) {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nnz) return;
-    const int p = __ldg(perm + q);
-    int lo = 0, hi = m;  // find the largest r in [0, m) with row_ptr[r] <= p
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(row_ptr + mid) <= p) lo = mid;
-        else hi = mid - 1;
-    }
-    col_ind_t[q] = lo;
+// rows[p] = the row of A holding nonzero p, for every p (a warp per row).
+__global__ void expand_rows_kernel(const int* __restrict__ row_ptr, int m, int* __restrict__ rows) {
+    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= m) return;
+    const int lane = threadIdx.x & 31;
+    const int p1 = __ldg(row_ptr + r + 1);
+    for (int p = __ldg(row_ptr + r) + lane; p < p1; p += 32) rows[p] = (int)r;
 }
 
 template <typename T>
@@ -445,6 +477,7 @@ int spmm_csr_transpose(int m, int k, long long nnz, const int* row_ptr, const in
     int* kbuf[2] = {reinterpret_cast<int*>(ws + L.off_k0), reinterpret_cast<int*>(ws + L.off_k1)};
     int* vtmp = reinterpret_cast<int*>(ws + L.off_v);
     int* hist = reinterpret_cast<int*>(ws + L.off_hist);
+    int* totals = reinterpret_cast<int*>(ws + L.off_tot);
     const int passes = radix_passes(k);
     const int* kin = col_ind;
     const int* vin = nullptr;  // payload of the first pass: the element index
@@ -456,10 +489,13 @@ int spmm_csr_transpose(int m, int k, long long nnz, const int* row_ptr, const in
         radix_hist_kernel<<<L.tiles, kSortThreads, 0, s>>>(kin, nnz, shift, L.tiles, hist);
         st = launched(cudaGetLastError());
         if (st != SPMM_OK) break;
-        exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(hist, (long long)kRadix * L.tiles);
+        digit_scan_kernel<<<kRadix, kScanThreads, 0, s>>>(hist, L.tiles, totals);
         st = launched(cudaGetLastError());
         if (st != SPMM_OK) break;
-        radix_scatter_kernel<<<L.tiles, kSortThreads, 0, s>>>(kin, vin, nnz, shift, L.tiles, hist, kout, vout);
+        digit_base_kernel<<<1, kRadix, 0, s>>>(totals);
+        st = launched(cudaGetLastError());
+        if (st != SPMM_OK) break;
+        radix_scatter_kernel<<<L.tiles, kSortThreads, 0, s>>>(kin, vin, nnz, shift, L.tiles, hist, totals, kout, vout);
         st = launched(cudaGetLastError());
         kin = kout;
         vin = vout;
@@ -468,9 +504,15 @@ int spmm_csr_transpose(int m, int k, long long nnz, const int* row_ptr, const in
         transpose_rowptr_kernel<<<(unsigned)(((long long)k + 1 + 255) / 256), 256, 0, s>>>(kin, nnz, k, row_ptr_t);
         st = launched(cudaGetLastError());
     }
-    if (st == SPMM_OK) {
-        transpose_rows_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(row_ptr, m, perm, nnz, col_ind_t);
+    if (st == SPMM_OK) {  // col_ind_t[q] = row of perm[q]: rows expanded into the free key buffer, then gathered
+        int* rows = kbuf[passes & 1];
+        expand_rows_kernel<<<(unsigned)(((long long)m * 32 + 255) / 256), 256, 0, s>>>(row_ptr, m, rows);
         st = launched(cudaGetLastError());
+        if (st == SPMM_OK) {
+            gather_values_kernel<int><<<(unsigned)std::min<long long>((nnz + 255) / 256, 152LL * 16), 256, 0, s>>>(
+                perm, nnz, rows, col_ind_t);
+            st = launched(cudaGetLastError());
+        }
     }
     if (own) {
         const cudaError_t e = cudaFreeAsync(ws, s);
