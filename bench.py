@@ -8,14 +8,18 @@ Section 5.4 mean-row-length rule recalibrated, plus a longest-row guard); the
 JSON line also reports the Section 5.4 rule's own pick and both families'
 times (``--alg`` overrides).  After the headline, the growth forms are
 measured: 16-bit storage (2M x 2M, n = 128), a GCN layer's forward and
-backward (500k nodes, n = 256) and a 2048-matrix batch in one graph-captured
-persistent launch.  All inputs are synthetic and seeded (gen/).
+backward (500k nodes, n = 256, with the transpose on its own) and a
+2048-matrix batch in graph-captured persistent launches.  All inputs are
+synthetic and seeded (gen/).
 
 Timing: inputs resident in HBM; L2 is flushed (a write of twice its size)
 before every step, outside the events; each call is bracketed by CUDA events on
 the launching stream.  ``e2e`` times the same step through ``spmm_csr_host``
-(host buffers; H2D of A and B, D2H of C inside the timed region).
-``--impl reference`` times the FP64 CPU oracle on a bounded row sample.
+(host buffers; H2D of A and B, D2H of C inside the timed region) next to the
+host link's own copy rates.  ``--impl reference`` times the FP64 CPU oracle on
+a bounded row sample.  ``--sweep aspect|density|spmv|tiling|selector`` runs one
+of the parameter sweeps instead (a JSON line per point), and ``--ingest-ncu``
+turns the recorded ncu traffic capture into the JSON the roofline reads.
 """
 from __future__ import annotations
 
