@@ -147,40 +147,67 @@ __global__ void digit_base_kernel(int* __restrict__ totals) {
     totals[tid] = before + x - v;
 }
 
-// Stable scatter of one radix pass.  A tile is consumed in rounds of 256
-// consecutive elements, thread t holding element t of the round; inside a
-// warp the rank among equal digits comes from __match_any_sync, across warps
-// from per-warp digit counts in shared memory, across rounds from a running
-// per-digit base.  Element order is therefore kept among equal digits.
-// payload_in == nullptr means the payload is the element's own index.
+// Stable scatter of one radix pass.  The tile is first sorted by digit in
+// shared memory (counts of the tile's digits, scanned into tile-local digit
+// offsets; elements placed in rounds of 256 consecutive elements, thread t
+// holding element t of the round, the rank among equal digits from
+// __match_any_sync inside a warp, per-warp digit counts across warps and a
+// running per-digit count across rounds), then written out in that order, so
+// a run of equal digits goes to consecutive global positions.  Element order
+// is kept among equal digits.  payload_in == nullptr means the payload is the
+// element's own index.
 __global__ void radix_scatter_kernel(const int* __restrict__ keys_in, const int* __restrict__ payload_in, long long n,
                                      int shift, int tiles, const int* __restrict__ offsets,
                                      const int* __restrict__ digit_base, int* __restrict__ keys_out,
                                      int* __restrict__ payload_out) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ int base[kRadix];
+    __shared__ int s_key[kSortTile];
+    __shared__ int s_pay[kSortTile];
+    __shared__ int local[kRadix];  // tile-local first position of each digit
+    __shared__ int run[kRadix];    // elements of each digit placed so far
     __shared__ int wcnt[kWarps][kRadix];
+    __shared__ int warp_sum[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    base[tid] = offsets[(long long)tid * tiles + blockIdx.x] + digit_base[tid];
+    const long long tile0 = (long long)blockIdx.x * kSortTile;
+    const int count = n - tile0 < kSortTile ? (int)(n - tile0) : kSortTile;
+    run[tid] = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
     __syncthreads();
+    for (int i = tid; i < count; i += kSortThreads) atomicAdd(&run[(__ldg(keys_in + tile0 + i) >> shift) & (kRadix - 1)], 1);
+    __syncthreads();
+    {  // exclusive scan of the tile's 256 digit counts (kSortThreads == kRadix)
+        const int v = run[tid];
+        int x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFullMask, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        local[tid] = before + x - v;
+        run[tid] = 0;
+    }
+    __syncthreads();
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int r = 0; r < kSortItems; ++r) {
-        const long long idx = (long long)blockIdx.x * kSortTile + (long long)r * kSortThreads + tid;
-        const bool valid = idx < n;
-        const int key = valid ? __ldg(keys_in + idx) : 0;
-        const int pay = valid ? (payload_in ? __ldg(payload_in + idx) : (int)idx) : 0;
+        const int i = r * kSortThreads + tid;
+        const bool valid = i < count;
+        const int key = valid ? __ldg(keys_in + tile0 + i) : 0;
+        const int pay = valid ? (payload_in ? __ldg(payload_in + tile0 + i) : (int)(tile0 + i)) : 0;
         const int d = valid ? (key >> shift) & (kRadix - 1) : kRadix + lane;  // invalid lanes match nobody
         const unsigned peers = __match_any_sync(kFullMask, d);
         const int rank = __popc(peers & lt_mask);
         if (valid && lane == 31 - __clz(peers)) wcnt[warp][d] = __popc(peers);
         __syncthreads();
         if (valid) {
-            int pos = base[d] + rank;
+            int pos = local[d] + run[d] + rank;
             for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            keys_out[pos] = key;
-            payload_out[pos] = pay;
+            s_key[pos] = key;
+            s_pay[pos] = pay;
         }
         __syncthreads();
         int tot = 0;
@@ -189,8 +216,17 @@ __global__ void radix_scatter_kernel(const int* __restrict__ keys_in, const int*
             tot += wcnt[w][tid];
             wcnt[w][tid] = 0;
         }
-        base[tid] += tot;
+        run[tid] += tot;
         __syncthreads();
+    }
+    // write out in tile order: element i of digit d goes to the digit's global run for this tile
+    local[tid] = offsets[(long long)tid * tiles + blockIdx.x] + digit_base[tid] - local[tid];
+    __syncthreads();
+    for (int i = tid; i < count; i += kSortThreads) {
+        const int key = s_key[i];
+        const int pos = local[(key >> shift) & (kRadix - 1)] + i;
+        keys_out[pos] = key;
+        payload_out[pos] = s_pay[i];
     }
 }
 
