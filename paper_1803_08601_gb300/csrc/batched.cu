@@ -263,6 +263,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     cudaGetDevice(&p->device);
     std::vector<MatDesc> descs(mats.size());
     std::vector<Item> items, tile_items;
+    std::vector<int> row_mats;  // matrices computed by row split
     std::vector<int> tile_mat;
     size_t carry_floats = 0, limit_entries = 0;
     size_t smem = 0;
@@ -300,10 +301,18 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
             smem = std::max(smem, merge_smem_bytes(d.W, d.ips));
         } else {
             d.num_tiles = 0;
-            const int chunk = kRowsPerGroupPerItem * (kThreads / d.W);
-            for (int sl = 0; sl < d.slabs; ++sl)
-                for (int r = 0; r < mt.m; r += chunk) items.push_back(Item{(int)b, sl << 1, r, std::min(mt.m, r + chunk)});
+            row_mats.push_back((int)b);
         }
+    }
+    // row-split chunks, largest matrices first: the big matrices' rows of B are then gathered
+    // while few other matrices compete for L2, and the small ones fill the tail of the launch
+    std::stable_sort(row_mats.begin(), row_mats.end(), [&](int x, int y) { return mats[x].nnz > mats[y].nnz; });
+    for (const int b : row_mats) {
+        const auto& mt = mats[b];
+        const MatDesc& d = descs[b];
+        const int chunk = kRowsPerGroupPerItem * (kThreads / d.W);
+        for (int sl = 0; sl < d.slabs; ++sl)
+            for (int r = 0; r < mt.m; r += chunk) items.push_back(Item{b, sl << 1, r, std::min(mt.m, r + chunk)});
     }
     p->n_row_items = (long long)items.size();
     items.insert(items.end(), tile_items.begin(), tile_items.end());
