@@ -456,7 +456,9 @@ def main():
             "config": {"workload": label, "m": m, "k": k, "nnz": nnz, "max_row": max_row, "n": ns, "alg": args.alg,
                        "tuning": tuning,
                        "replicas": world, "l2_flush": "2x L2 write before every step", "parallelism": "replicas"},
-            "roofline": roofline, "gpu_launches": int(launches)}
+            "roofline": roofline, "gpu_launches": int(launches),
+            "step_ms_stats": {"median": float(statistics.median(step_ms)), "min": float(min(step_ms)),
+                              "max": float(max(step_ms)), "steps": len(step_ms)}}
     cs = clk.summary()
     if cs:
         line["clocks"] = cs
