@@ -72,7 +72,8 @@ def test_sddmm(gpu_lib, name, n):
 @pytest.mark.parametrize("n", [64, 256, 1024])
 @pytest.mark.parametrize("dt,out_f32", [("bf16", False), ("bf16", True), ("f16", False), ("f16", True)])
 def test_sddmm_16bit(gpu_lib, dt, out_f32, n):
-    """n = 64 takes the lane-group kernel; 256 and 1024 the warp kernel with dC rows in registers."""
+    """n = 64 (8 vectors of 16-bit values per row) takes the lane-group kernel; 256 and 1024 the warp
+    kernel with dC rows in registers."""
     import torch
 
     rp, ci, v, k = structure("power_law")
