@@ -524,17 +524,21 @@ def e2e(pkg, torch, a, ns, Bs, args, tuning):
     for n in ns:
         pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning)
     torch.cuda.synchronize()
-    reps = max(2, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    reps = max(5, min(args.steps, 10))
+    steps_s = []
+    for _ in range(reps):  # every call synchronises: each step is timed on its own, the median reported
+        t0 = time.perf_counter()
         for n in ns:
             pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning)
-    t = (time.perf_counter() - t0) / reps
+        steps_s.append(time.perf_counter() - t0)
+    t = statistics.median(steps_s)
     flops = sum(2.0 * a.nnz * n for n in ns)
     link = host_link(torch)
     bound_ms = (h2d + d2h) / (link["duplex_gbs"] * 1e9) * 1e3
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3, "api": "spmm_csr_host", "link": link,
+            "ms_per_step": t * 1e3, "step_ms": {"median": t * 1e3, "min": min(steps_s) * 1e3,
+                                                "max": max(steps_s) * 1e3, "steps": reps},
+            "api": "spmm_csr_host", "link": link,
             "link_bound_ms": bound_ms, "frac_of_link_bound": bound_ms / (t * 1e3)}
 
 

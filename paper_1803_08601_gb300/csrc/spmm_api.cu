@@ -627,8 +627,18 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
         off_val[c] = total;
         total += align256((size_t)cnnz * sv);
     }
+    // one merge workspace, lent to every block's call in turn (they run in order on `stream`)
+    size_t ws_need = 0;
+    if (alg == SPMM_ALG_MERGE)
+        for (int c = 0; c < chunks; ++c)
+            for (int j = 0; j < slabs; ++j) {
+                const long long cw = std::min<long long>(w, n - j * w);
+                ws_need = std::max(ws_need, spmm_csr_workspace_size(r[c + 1] - r[c], k, (int)cw,
+                                                                    row_ptr[r[c + 1]] - row_ptr[r[c]], alg, b_type, &t));
+            }
     const size_t off_B = total, off_C = off_B + align256((size_t)k * ldb_d * sb);
-    total = off_C + align256((size_t)m * ldc_d * sc);
+    const size_t off_ws = off_C + align256((size_t)m * ldc_d * sc);
+    total = off_ws + align256(ws_need);
     void* mem = nullptr;
     cudaError_t e = cudaMallocAsync(&mem, total, s);
     if (e != cudaSuccess) return SPMM_ERR_ALLOC;
@@ -689,8 +699,8 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
             if (st == SPMM_OK && rows > 0)
                 st = spmm_csr_ex(rows, k, (int)cw, cnnz, rp_c, reinterpret_cast<const int*>(base + off_col[c]),
                                  base + off_val[c], vals_type, d_B + c0 * sb,
-                                 b_type, ldb_d, d_C + ((size_t)r[c] * ldc_d + c0) * sc, c_type, ldc_d, alg, &t, nullptr,
-                                 0, nullptr, stream);
+                                 b_type, ldb_d, d_C + ((size_t)r[c] * ldc_d + c0) * sc, c_type, ldc_d, alg, &t,
+                                 ws_need ? base + off_ws : nullptr, ws_need, nullptr, stream);
             cudaEvent_t done = e_c[(size_t)j * chunks + c];
             if (st == SPMM_OK) st = cuda_status(cudaEventRecord(done, s));
             if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, done, 0));
