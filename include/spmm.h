@@ -246,6 +246,22 @@ int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, c
                   long long ldc, int alg, const spmm_tuning_t *tuning, void *stream);
 
 /*
+ * spmm_csr_host without the final synchronisation (no counterpart in the
+ * paper): the copies and kernels are queued and the call returns; C holds the
+ * result once `stream` has been synchronised (or an event recorded on it after
+ * the call has completed), and work queued on `stream` after the call runs
+ * after C has arrived.  row_ptr is read on the host during the call; every
+ * host buffer must stay valid, and A and B unmodified, until then.  With
+ * pinned host buffers, back-to-back calls overlap: a call's uploads run while
+ * the previous call's last blocks of C are still coming down.  Arguments,
+ * pipelining and errors as in spmm_csr_host; an error of a queued copy or
+ * kernel is reported by the synchronisation, not by this call.
+ */
+int spmm_csr_host_async(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
+                        int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,
+                        long long ldc, int alg, const spmm_tuning_t *tuning, void *stream);
+
+/*
  * Self-test of the bounded device-side wait used by the merge kernel's
  * shared-memory staging: one CTA waits on an mbarrier phase that nothing
  * completes, for at most limit_ns nanoseconds of device time (clamped to

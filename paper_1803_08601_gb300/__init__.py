@@ -9,7 +9,7 @@ Two layers:
 
 * the C entry points under their C names (``spmm_csr``, ``spmm_csr_ex``,
   ``spmm_csr_workspace_size``, ``spmm_select_alg``, ``spmm_merge_partition``,
-  ``spmm_csr_host``, ...), taking integers for pointers and streams exactly as
+  ``spmm_csr_host``, ``spmm_csr_host_async``, ...), taking integers for pointers and streams exactly as
   the C functions do;
 * tensor helpers (``spmm``, ``merge_partition``, ``spmm_host``) that take
   torch CUDA tensors, use torch only for device memory and the current stream,
@@ -68,6 +68,7 @@ _SIGNATURES = {
     "spmm_csr_workspace_size": ([_i, _i, _i, _ll, _i, _i, _TP], _sz),
     "spmm_merge_partition": ([_i, _ll, _vp, _i, _i, _vp, _vp], _i),
     "spmm_csr_host": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
+    "spmm_csr_host_async": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
     "spmm_debug_bounded_wait": ([_vp, _ll, _vp], _i),
     "spmm_csr_noalloc": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _vp], _i),
     "spmm_csr_static_scratch_bytes": ([], _sz),
@@ -170,6 +171,12 @@ def spmm_csr_host(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C,
                   stream) -> int:
     return load().spmm_csr_host(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg,
                                 _tuning_ptr(tuning), stream)
+
+
+def spmm_csr_host_async(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                        stream) -> int:
+    return load().spmm_csr_host_async(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc,
+                                      alg, _tuning_ptr(tuning), stream)
 
 
 def spmm_debug_bounded_wait(d_status, limit_ns, stream) -> int:
@@ -332,18 +339,23 @@ def merge_partition(row_ptr, items_per_tile: int, nnz: int | None = None, stream
     return lim
 
 
-def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None):
+def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None, wait=True):
     """C = A @ B with every operand in host memory (CPU tensors, ideally pinned):
-    the library copies to the device, computes, copies back and synchronises."""
+    the library copies to the device, computes and copies back.  With
+    ``wait=True`` (``spmm_csr_host``) the call returns once C is filled; with
+    ``wait=False`` (``spmm_csr_host_async``) it returns once the work is queued,
+    and C is filled when ``stream`` (default: torch's current stream) has been
+    synchronised; the operands must stay alive and A, B unchanged until then."""
     for t in (row_ptr, col_ind, vals, B, C):
         if t.is_cuda:
             raise ValueError("spmm_host takes host tensors")
     m = row_ptr.numel() - 1
     k, n = B.shape
-    st = spmm_csr_host(m, k, n, row_ptr.data_ptr(), col_ind.data_ptr(), vals.data_ptr(), dtype_code(vals.dtype),
-                       B.data_ptr(), dtype_code(B.dtype), B.stride(0), C.data_ptr(), dtype_code(C.dtype), C.stride(0),
-                       alg_code(alg), tuning, _stream_handle(stream))
-    _check(st, "spmm_csr_host")
+    fn, name = (spmm_csr_host, "spmm_csr_host") if wait else (spmm_csr_host_async, "spmm_csr_host_async")
+    st = fn(m, k, n, row_ptr.data_ptr(), col_ind.data_ptr(), vals.data_ptr(), dtype_code(vals.dtype),
+            B.data_ptr(), dtype_code(B.dtype), B.stride(0), C.data_ptr(), dtype_code(C.dtype), C.stride(0),
+            alg_code(alg), tuning, _stream_handle(stream))
+    _check(st, name)
     return C
 
 

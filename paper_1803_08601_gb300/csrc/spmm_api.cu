@@ -268,6 +268,39 @@ void keep_pool_memory() {
     done[dev] = true;
 }
 
+// Staging memory of the host-buffer entries: a pool of their own per device,
+// created once.  A call's buffer is allocated on the upload stream and freed
+// on the download stream; the pool may reuse it for a later call once the
+// free has completed, but never by making the later call's uploads wait on
+// the earlier call's downloads (the default pool may insert such a wait),
+// which would serialise back-to-back asynchronous calls.  Freed memory stays
+// cached until exit.
+cudaMemPool_t host_staging_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        unsigned long long thr = ~0ull;
+        int no = 0;
+        if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess ||
+            cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return nullptr;
+        }
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 // Two copy streams per device (host-to-device, device-to-host), created once.
 bool copy_streams(cudaStream_t* up, cudaStream_t* down) {
     static std::mutex mu;
@@ -563,9 +596,11 @@ int spmm_csr(int m, int k, int n, const int* row_ptr, const int* col_ind, const 
                        nullptr, nullptr, 0, nullptr, stream);
 }
 
-int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
-                  const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
-                  const spmm_tuning_t* tuning, void* stream) {
+// The host-buffer product, enqueued on `stream` and the two copy streams; with `wait` the call
+// returns only when C is in host memory.
+static int host_product(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                        const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
+                        const spmm_tuning_t* tuning, void* stream, bool wait) {
     if (m < 0 || k < 0 || n < 0) return SPMM_ERR_INVALID_VALUE;
     if (m > 0 && !row_ptr) return SPMM_ERR_INVALID_VALUE;
     const long long nnz = m > 0 ? row_ptr[m] : 0;
@@ -639,19 +674,35 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
     const size_t off_B = total, off_C = off_B + align256((size_t)k * ldb_d * sb);
     const size_t off_ws = off_C + align256((size_t)m * ldc_d * sc);
     total = off_ws + align256(ws_need);
+    cudaMemPool_t pool = host_staging_pool();
+    if (!pool) return SPMM_ERR_CUDA;
+    std::vector<cudaEvent_t> ev(3 + chunks + slabs + (size_t)slabs * chunks, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    auto destroy_events = [&] {
+        for (auto& x : ev)  // an event still pending is released once it completes
+            if (x) cudaEventDestroy(x);
+    };
+    if (e != cudaSuccess) {
+        destroy_events();
+        return cuda_status(e);
+    }
+    // The buffer is allocated in the upload stream's order, so the uploads need no other wait;
+    // compute and downloads reach it only through events recorded after those uploads.
     void* mem = nullptr;
-    cudaError_t e = cudaMallocAsync(&mem, total, s);
-    if (e != cudaSuccess) return SPMM_ERR_ALLOC;
+    e = cudaMallocFromPoolAsync(&mem, total, pool, up);
+    if (e != cudaSuccess) {
+        destroy_events();
+        return SPMM_ERR_ALLOC;
+    }
     unsigned char* base = static_cast<unsigned char*>(mem);
     unsigned char* d_B = base + off_B;
     unsigned char* d_C = base + off_C;
-    std::vector<cudaEvent_t> ev(1 + chunks + slabs + (size_t)slabs * chunks, nullptr);
-    for (auto& x : ev)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-    cudaEvent_t e_alloc = ev[0];
-    cudaEvent_t* e_a = ev.data() + 1;                // chunk c of A uploaded
-    cudaEvent_t* e_b = ev.data() + 1 + chunks;       // slab j of B uploaded
-    cudaEvent_t* e_c = ev.data() + 1 + chunks + slabs;  // block (j, c) of C computed
+    cudaEvent_t e_up = ev[0], e_s = ev[1], e_end = ev[2];  // uploads, compute, downloads + free done
+    cudaEvent_t* e_a = ev.data() + 3;                  // chunk c of A uploaded
+    cudaEvent_t* e_b = ev.data() + 3 + chunks;         // slab j of B uploaded
+    cudaEvent_t* e_c = ev.data() + 3 + chunks + slabs;  // block (j, c) of C computed
     auto upload_b = [&](int j) {
         const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
         cudaError_t x = cudaSuccess;
@@ -663,9 +714,7 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
         if (x == cudaSuccess) x = cudaEventRecord(e_b[j], up);
         return x;
     };
-    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_alloc, 0);
-    if (e == cudaSuccess) e = upload_b(0);
+    e = upload_b(0);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         const long long p0 = row_ptr[r[c]], p1 = row_ptr[r[c + 1]];
         e = cudaMemcpyAsync(base + off_rp[c], row_ptr + r[c], (size_t)(r[c + 1] - r[c] + 1) * 4, cudaMemcpyHostToDevice,
@@ -714,16 +763,45 @@ int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, c
             }
         }
     }
-    // release after every stream that touched the buffer is done with it
-    cudaStreamSynchronize(up);
-    cudaStreamSynchronize(down);
-    e = cudaFreeAsync(mem, s);
-    if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
-    e = cudaStreamSynchronize(s);
-    if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
-    for (auto& x : ev)
-        if (x) cudaEventDestroy(x);
+    // Free the buffer in the download stream's order once every stream that touched it is done
+    // with it, then make `stream` wait for that point: work queued on `stream` after this call,
+    // and a synchronisation of it, see C in host memory.  Nothing here blocks the host, so the
+    // next call's uploads can overlap this call's last downloads.
+    bool freed = false;
+    cudaError_t f = cudaEventRecord(e_up, up);
+    if (f == cudaSuccess) f = cudaEventRecord(e_s, s);
+    if (f == cudaSuccess) f = cudaStreamWaitEvent(down, e_up, 0);
+    if (f == cudaSuccess) f = cudaStreamWaitEvent(down, e_s, 0);
+    if (f == cudaSuccess) freed = (f = cudaFreeAsync(mem, down)) == cudaSuccess;
+    if (f == cudaSuccess) f = cudaEventRecord(e_end, down);
+    if (f == cudaSuccess) f = cudaStreamWaitEvent(s, e_end, 0);
+    if (f != cudaSuccess) {  // the stream order is broken: drain all three streams instead
+        cudaStreamSynchronize(up);
+        cudaStreamSynchronize(down);
+        if (!freed) cudaFreeAsync(mem, s);
+        cudaStreamSynchronize(s);
+        if (st == SPMM_OK) st = cuda_status(f);
+    }
+    destroy_events();
+    if (wait) {
+        e = cudaStreamSynchronize(s);
+        if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+    }
     return st;
+}
+
+int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                  const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
+                  const spmm_tuning_t* tuning, void* stream) {
+    return host_product(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                        stream, true);
+}
+
+int spmm_csr_host_async(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                        const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
+                        const spmm_tuning_t* tuning, void* stream) {
+    return host_product(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
+                        stream, false);
 }
 
 int spmm_debug_bounded_wait(int* d_status, long long limit_ns, void* stream) {

@@ -336,6 +336,44 @@ def test_host_entry_row_chunks(gpu_lib, n):
         check(C.numpy(), rp, ci, v, B)
 
 
+def test_host_async_back_to_back(gpu_lib):
+    """spmm_csr_host_async: products of several widths, families and matrices
+    (one large enough for four row chunks of A) queued back to back with no
+    synchronisation in between, then one synchronisation of the stream; a copy
+    of C queued on the stream after a call sees its result; a second round of
+    the same calls (staging memory reused) gives the same bits."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(21)
+    lens = rng.integers(0, 48, 200_000)
+    lens[77_777] = 250_000
+    big = csr_arrays(lens, 300_000, 22)
+    assert len(big[0]) * 4 + 8 * int(big[0][-1]) >= 32 << 20  # A's bytes: four chunks of at least 8 MB
+    *small, k_small = structure("power_law")
+    cases = [(big, 300_000, 8, "merge"), (small, k_small, 64, "row_split"), (big, 300_000, 128, "auto_gb300"),
+             (small, k_small, 13, "merge"), (big, 300_000, 32, "row_split")]
+    Bs = [torch.from_numpy(gen.normal_matrix(k, n, 23 + i)).pin_memory() for i, (_, k, n, _) in enumerate(cases)]
+    As = [tuple(torch.from_numpy(x).pin_memory() for x in a) for a, _, _, _ in cases]
+    stream = torch.cuda.current_stream()
+    results = []
+    for round_ in range(2):
+        Cs = [torch.full((len(a[0]) - 1, n), float("nan")).pin_memory() for a, _, n, _ in cases]
+        seen = None
+        for i, ((a, k, n, alg), (rp, ci, v)) in enumerate(zip(cases, As)):
+            pkg.spmm_host(rp, ci, v, Bs[i], Cs[i], alg=alg, wait=False)
+            if i == 1:  # queued after the call on the same stream: must see C
+                seen = Cs[i].to("cuda", non_blocking=True)
+        stream.synchronize()
+        if round_ == 0:
+            for (a, k, n, alg), B, C in zip(cases, Bs, Cs):
+                check(C.numpy(), *a, B.numpy())
+        assert torch.equal(seen.cpu(), Cs[1])
+        results.append(Cs)
+    for c0, c1 in zip(*results):
+        assert torch.equal(c0, c1)
+
+
 def test_host_entry_few_long_rows(gpu_lib):
     """Three rows of two million nonzeros: at most as many chunks as rows."""
     import torch

@@ -117,6 +117,38 @@ def test_argument_checks_return_before_any_device_work(lib):
     assert pkg.spmm_debug_bounded_wait(None, 1000, None) == pkg.ERR_INVALID_VALUE
 
 
+def test_host_entries_check_arguments_on_the_host(lib):
+    """spmm_csr_host and spmm_csr_host_async read row_ptr[m] on the host and
+    reject bad arguments before any CUDA call; empty products return at once."""
+    import numpy as np
+
+    rp = np.array([0, 1, 2, 3, 4], dtype=np.int32)
+    ci = np.arange(4, dtype=np.int32)
+    v = np.ones(4, dtype=np.float32)
+    B = np.ones((4, 8), dtype=np.float32)
+    C = np.zeros((4, 8), dtype=np.float32)
+    F = pkg.F32
+    good = dict(m=4, k=4, n=8, row_ptr=rp.ctypes.data, col_ind=ci.ctypes.data, vals=v.ctypes.data, vals_type=F,
+                B=B.ctypes.data, b_type=F, ldb=8, C=C.ctypes.data, c_type=F, ldc=8, alg=pkg.ALG_MERGE, tuning=None,
+                stream=None)
+    for fn in (pkg.spmm_csr_host, pkg.spmm_csr_host_async):
+        def call(**kw):
+            a = dict(good)
+            a.update(kw)
+            return fn(*a.values())
+
+        assert call(m=-1) == pkg.ERR_INVALID_VALUE
+        assert call(row_ptr=None) == pkg.ERR_INVALID_VALUE
+        assert call(ldb=4) == pkg.ERR_INVALID_VALUE
+        assert call(ldc=7) == pkg.ERR_INVALID_VALUE
+        assert call(alg=9) == pkg.ERR_INVALID_VALUE
+        assert call(col_ind=None) == pkg.ERR_INVALID_VALUE
+        assert call(vals_type=F, b_type=pkg.F16) == pkg.ERR_UNSUPPORTED
+        assert call(m=0) == pkg.OK
+        assert call(n=0) == pkg.OK
+        assert np.all(C == 0)
+
+
 def test_semiring_argument_checks(lib):
     good = dict(m=4, k=4, n=4, nnz=4, row_ptr=8, col_ind=16, vals=32, B=64, ldb=4, C=128, ldc=4,
                 semiring=pkg.SEMIRING_MIN_PLUS, alg=0, tuning=None, workspace=None, workspace_bytes=0, d_status=None,
