@@ -529,9 +529,10 @@ def e2e(pkg, torch, a, ns, Bs, args, tuning):
     reps = max(5, min(args.steps, 10))
 
     def timed(wait):
-        for n in ns:
-            pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning, wait=wait)
-        stream.synchronize()
+        for _ in range(max(args.warmup, 3)):  # warm-up steps (the staging pool grows to its steady size)
+            for n in ns:
+                pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning, wait=wait)
+            stream.synchronize()
         steps_s = []
         for _ in range(reps):  # each step is timed on its own, the median reported
             t0 = time.perf_counter()
@@ -549,7 +550,8 @@ def e2e(pkg, torch, a, ns, Bs, args, tuning):
     bound_ms = (h2d + d2h) / (link["duplex_gbs"] * 1e9) * 1e3
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3, "step_ms": {"median": t * 1e3, "min": min(steps_s) * 1e3,
-                                                "max": max(steps_s) * 1e3, "steps": reps},
+                                                "max": max(steps_s) * 1e3, "steps": reps,
+                                                "all": [round(x * 1e3, 3) for x in steps_s]},
             "api": "spmm_csr_host_async",
             "sync_calls": {"api": "spmm_csr_host", "ms_per_step": statistics.median(sync_s) * 1e3,
                            "min": min(sync_s) * 1e3, "max": max(sync_s) * 1e3,

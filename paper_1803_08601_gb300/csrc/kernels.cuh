@@ -528,7 +528,11 @@ __global__ void __launch_bounds__(256) merge_kernel_wide(MergeArgs a) {
 // carry-out belongs to the same row R (a row spanning several tiles), the row
 // is finished by the tile right after the run, which left R's remaining
 // partial sum in head[]; C[R] = carries (in tile order) + head, rounded once.
-// One warp per tile (grid-stride); only run heads do work, lanes stride n.
+// One warp per tile (grid-stride); only run heads do work.  Lanes stride n in
+// 16-byte vectors of four columns when n allows (so one pass covers up to 128
+// columns), with up to 16 of a run's tiles loaded at once: the long runs of
+// rows that span many tiles are the kernel's critical path.  Each column is
+// still summed in tile order.
 template <typename TC, typename SR = PlusTimes>
 __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int* __restrict__ head_row,
                                    const float* __restrict__ carry, const float* __restrict__ head, int num_tiles,
@@ -554,12 +558,43 @@ __global__ void merge_fixup_kernel(const int* __restrict__ carry_row, const int*
             if (lane == 0) report(status, SPMM_ERR_BAD_CSR);
             continue;
         }
-        for (int c = lane; c < n; c += 32) {
-            float sum = SR::identity();
-#pragma unroll 8
-            for (int t = i; t <= j; ++t) sum = SR::add(sum, carry[(size_t)t * n + c]);
-            sum = SR::add(sum, head[(size_t)(j + 1) * n + c]);
-            C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
+        if ((n & 3) == 0) {  // rows of carry / head are 16-byte aligned
+            auto add4 = [](float4 s, float4 x) {
+                return make_float4(SR::add(s.x, x.x), SR::add(s.y, x.y), SR::add(s.z, x.z), SR::add(s.w, x.w));
+            };
+            for (int c = lane * 4; c < n; c += 128) {
+                float4 sum = make_float4(SR::identity(), SR::identity(), SR::identity(), SR::identity());
+                int t = i;
+                for (; t + 15 <= j; t += 16) {  // 16 loads in flight, then the adds in tile order
+                    float4 x[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) x[u] = *reinterpret_cast<const float4*>(carry + (size_t)(t + u) * n + c);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) sum = add4(sum, x[u]);
+                }
+                for (; t <= j; ++t) sum = add4(sum, *reinterpret_cast<const float4*>(carry + (size_t)t * n + c));
+                const float4 h = *reinterpret_cast<const float4*>(head + (size_t)(j + 1) * n + c);
+                TC* out = C + (long long)R * ldc + c;
+                out[0] = Elem<TC>::from_f(SR::add(sum.x, h.x));
+                out[1] = Elem<TC>::from_f(SR::add(sum.y, h.y));
+                out[2] = Elem<TC>::from_f(SR::add(sum.z, h.z));
+                out[3] = Elem<TC>::from_f(SR::add(sum.w, h.w));
+            }
+        } else {
+            for (int c = lane; c < n; c += 32) {
+                float sum = SR::identity();
+                int t = i;
+                for (; t + 15 <= j; t += 16) {
+                    float x[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) x[u] = carry[(size_t)(t + u) * n + c];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) sum = SR::add(sum, x[u]);
+                }
+                for (; t <= j; ++t) sum = SR::add(sum, carry[(size_t)t * n + c]);
+                sum = SR::add(sum, head[(size_t)(j + 1) * n + c]);
+                C[(long long)R * ldc + c] = Elem<TC>::from_f(sum);
+            }
         }
     }
 }

@@ -151,6 +151,37 @@ def test_gb300_selector_picks_merge_for_heavy_tail(gpu_lib):
     check(C.cpu().numpy(), rp, ci, v, B)
 
 
+@pytest.mark.parametrize("n,tuning", [(1, dict(items_per_subwarp=4)), (1, None), (13, dict(items_per_subwarp=5)),
+                                      (64, dict(items_per_subwarp=4, column_slabs=4)), (128, None)])
+def test_rows_crossing_many_tiles_reuse_one_workspace(gpu_lib, n, tuning):
+    """Rows that span up to thousands of merge tiles (in every column slab),
+    the last of them running to the end of the path, finished by the fix-up.
+    Integer values make the result exact in any order; the status word stays
+    clear; one workspace reused by back-to-back calls on the stream (each call
+    rewrites every entry it reads) gives the same bits every time."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(5)
+    lens = rng.integers(0, 6, 3000)
+    lens[[7, 1500, 2999]] = [40_000, 25_000, 60_000]  # the last row runs to the end of the path
+    lens[100:200] = 0
+    rp, ci, v = csr_arrays(lens, 70_000, 31, int_vals=True)
+    B = rng.integers(-3, 4, size=(70_000, n)).astype(np.float32)
+    ref = oracle.spmm(rp, ci, v, B).astype(np.float32)
+    d_rp, d_ci, d_v, d_B = to_dev(torch, rp, ci, v, B)
+    nnz = int(rp[-1])
+    ws = torch.empty(pkg.workspace_size(len(rp) - 1, 70_000, n, nnz, "merge", tuning=tuning), dtype=torch.uint8,
+                     device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = [pkg.spmm(d_rp, d_ci, d_v, d_B, alg="merge", nnz=nnz, tuning=tuning, workspace=ws, status=status)
+            for _ in range(3)]
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    for C in outs:
+        assert np.array_equal(C.cpu().numpy(), ref)
+
+
 def test_launch_counts(gpu_lib):
     import torch
 
