@@ -237,9 +237,10 @@ int spmm_merge_partition(int m, long long nnz, const int *row_ptr, int items_per
  * (SPMM_ALG_AUTO_GB300 without tuning->max_row_len scans the host row_ptr for
  * the longest row).  Copies and compute are pipelined: B and C in column
  * slabs, A in up to four row chunks, so that the first block is computed as
- * soon as its pieces are on the device.  Device buffers are obtained
- * stream-ordered and released before return.  Pinned (page-locked) host
- * buffers make the copies asynchronous DMA.
+ * soon as its pieces are on the device.  Device buffers come stream-ordered
+ * from a memory pool of the library's own (one per device; freed memory stays
+ * cached in it until exit) and are released before return.  Pinned
+ * (page-locked) host buffers make the copies asynchronous DMA.
  */
 int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
                   int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,
@@ -248,9 +249,9 @@ int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, c
 /*
  * spmm_csr_host without the final synchronisation (no counterpart in the
  * paper): the copies and kernels are queued and the call returns; C holds the
- * result once `stream` has been synchronised (or an event recorded on it after
- * the call has completed), and work queued on `stream` after the call runs
- * after C has arrived.  row_ptr is read on the host during the call; every
+ * result once `stream` has been synchronised, or once an event recorded on
+ * `stream` after the call has completed, and work queued on `stream` after the
+ * call runs after C has arrived.  row_ptr is read on the host during the call; every
  * host buffer must stay valid, and A and B unmodified, until then.  With
  * pinned host buffers, back-to-back calls overlap: a call's uploads run while
  * the previous call's last blocks of C are still coming down.  Arguments,
