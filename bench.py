@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 import gen  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+ALG_NAME = {1: "row_split", 2: "merge", 5: "hybrid"}  # spmm_alg_t codes of the families
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -55,7 +56,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="power_law", choices=["power_law", "plain"])
     p.add_argument("--n", type=int, nargs="*", default=None, help="dense widths (default 8 32 64 128)")
-    p.add_argument("--alg", default="auto_gb300", choices=["auto_gb300", "auto", "row_split", "merge"])
+    p.add_argument("--alg", default="auto_gb300", choices=["auto_gb300", "auto", "row_split", "merge", "hybrid"])
     p.add_argument("--no-extras", action="store_true", help="skip e2e, cpu_baseline and per-algorithm breakdown "
                    "(the growth forms are controlled by --forms)")
     p.add_argument("--no-clocks", action="store_true")
@@ -386,7 +387,8 @@ def main():
     gb300_pick = {n: pkg.spmm_select_alg_gb300(m, nnz, max_row, n, pkg.F32) for n in ns}
     alg_of = {n: {"auto": paper_pick[n], "auto_gb300": gb300_pick[n]}.get(args.alg, pkg.alg_code(args.alg)) for n in ns}
     tuning_ws = json.loads(args.tuning) if args.tuning else None
-    ws_bytes = max(pkg.workspace_size(m, k, n, nnz, pkg.ALG_MERGE, tuning=tuning_ws) for n in ns)
+    ws_bytes = max(pkg.workspace_size(m, k, n, nnz, al, tuning=tuning_ws)
+                   for n in ns for al in (pkg.ALG_MERGE, pkg.ALG_ROW_SPLIT_HYBRID))
     ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.float32, device=dev)
@@ -437,7 +439,8 @@ def main():
     # dominant kernel: the (alg, n) call with the largest share of the step; roofline of its family
     comp = {n: compulsory_bytes(m, nnz, k, n) for n in ns}
     mean_call = {n: float(statistics.mean(per_call[n])) for n in ns}
-    dom_alg = {pkg.ALG_ROW_SPLIT: "rowsplit_kernel", pkg.ALG_MERGE: "merge_kernel"}
+    dom_alg = {pkg.ALG_ROW_SPLIT: "rowsplit_kernel", pkg.ALG_MERGE: "merge_kernel",
+               pkg.ALG_ROW_SPLIT_HYBRID: "rowsplit_hybrid_kernel"}
     fam = max({alg_of[n] for n in ns}, key=lambda al: sum(mean_call[n] for n in ns if alg_of[n] == al))
     fam_ns = [n for n in ns if alg_of[n] == fam]
     achieved = sum(comp[n] for n in fam_ns) / (sum(mean_call[n] for n in fam_ns) * 1e-3) / 1e9
@@ -447,7 +450,7 @@ def main():
                 "algorithmic_bytes": "compulsory: (m+1)*4 + nnz*8 + k*n*4 + m*n*4 per call, summed over n",
                 "per_n": {str(n): {"ms": mean_call[n], "gb_s": comp[n] / (mean_call[n] * 1e-3) / 1e9,
                                    "gflops": 2.0 * nnz * n / (mean_call[n] * 1e-3) / 1e9,
-                                   "alg": "merge" if alg_of[n] == pkg.ALG_MERGE else "row_split"} for n in ns},
+                                   "alg": ALG_NAME[alg_of[n]]} for n in ns},
                 "gather_aware": gather_aware(dom_alg[fam], label, m, nnz, k, fam_ns, mean_call, peak, l2),
                 "l2_bytes": l2}
 
@@ -465,9 +468,8 @@ def main():
     if cs:
         line["clocks"] = cs
 
-    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
-    line["selector"] = {"paper_section_5_4": {str(n): name[paper_pick[n]] for n in ns},
-                        "gb300": {str(n): name[gb300_pick[n]] for n in ns}}
+    line["selector"] = {"paper_section_5_4": {str(n): ALG_NAME[paper_pick[n]] for n in ns},
+                        "gb300": {str(n): ALG_NAME[gb300_pick[n]] for n in ns}}
     if rank == 0 and not args.no_extras:
         line["breakdown"] = breakdown(pkg, torch, one, ns, nnz, comp, args.steps, flush, stream)
         line["e2e"] = e2e(pkg, torch, a, ns, Bs, args, tuning)
@@ -494,7 +496,7 @@ def main():
 def breakdown(pkg, torch, one, ns, nnz, comp, steps, flush, stream):
     """GFLOP/s and compulsory GB/s of each algorithm family at every n (same timing rules)."""
     out = {}
-    for alg in ("row_split", "merge"):
+    for alg in ("row_split", "merge", "hybrid"):
         out[alg] = {}
         for n in ns:
             for _ in range(2):
@@ -754,7 +756,7 @@ def run_sweep(args):
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4 + 1024, device=dev)
     reps = max(3, min(args.steps, 5))
     n = 64
-    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    name = ALG_NAME
     if args.sweep == "aspect":
         # dense matrices stored as CSR, from 2 rows of 2^23 nonzeros to 2^23 rows of 2 (the paper's Fig. 1 / Fig. 4)
         total = 1 << 24
@@ -848,7 +850,7 @@ def run_selector_sweep(pkg, torch, dev, flush, stream, reps):
     Poisson lengths, power-law lengths with density exponent 2 capped at 10^5) and mean lengths
     2-64, at n = 8, 32, 64, 128; each point records the two times, the Section 5.4 rule's pick,
     the GB300 selector's pick and each pick's time relative to the faster family (1 = right)."""
-    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    name = ALG_NAME
     m = k = 1_000_000
     Bs = {n: torch.randn(k, n, device=dev, generator=torch.Generator(device=dev).manual_seed(300 + n))
           for n in (8, 32, 64, 128)}
@@ -896,7 +898,7 @@ def run_spmv_sweep(pkg, torch, dev, flush, stream, reps):
             ("uniform_4Mx4M_4", lambda: gen.uniform_rows(4_000_000, 4_000_000, 4, gen.SEED_BASE + 81)),
             ("uniform_2Mx2M_32", lambda: gen.uniform_rows(2_000_000, 2_000_000, 32, gen.SEED_BASE + 82)),
             ("uniform_250kx250k_64", lambda: gen.uniform_rows(250_000, 250_000, 64, gen.SEED_BASE + 83))]
-    name = {pkg.ALG_ROW_SPLIT: "row_split", pkg.ALG_MERGE: "merge"}
+    name = ALG_NAME
     for label, make in mats:
         a = make()
         m, k, nnz = a.m, a.k, a.nnz

@@ -56,7 +56,7 @@ typedef enum {
     SPMM_ALG_AUTO_GB300 = 3, /* mean row length recalibrated on GB300 plus a
                                longest-row guard against Type 1 imbalance
                                (Section 3.2); see spmm_select_alg_gb300      */
-    SPMM_ALG_TILED = 4       /* row blocks of A times k-panels of B held in
+    SPMM_ALG_TILED = 4,      /* row blocks of A times k-panels of B held in
                                shared memory: the tiling of A and B that
                                Section 6 proposes for denser matrices.  Rows
                                must list their columns in increasing order
@@ -66,6 +66,14 @@ typedef enum {
                                the call runs the row split.  Measured slower
                                than the row split on GB300 at every density
                                tried; no selector picks it               */
+    SPMM_ALG_ROW_SPLIT_HYBRID = 5 /* row split whose granularity (Section 4.1)
+                               follows the row: rows of at most
+                               tuning->long_row_len nonzeros keep their lane
+                               group; longer rows (the Type 1 imbalance of
+                               Section 3.2) are queued on the device and cut
+                               into segments of a warp each, whose partial
+                               sums are added in segment order.  Needs a
+                               workspace (spmm_csr_workspace_size)       */
 } spmm_alg_t;
 
 typedef enum {
@@ -94,7 +102,10 @@ typedef struct {
                                 a slab of B resident in L2                              */
     int items_per_subwarp;   /* merge based: merge-path items (rows + nonzeros) per
                                 lane group; a tile holds 256 / lanes_per_row groups     */
-    int reserved;            /* set to 0                                               */
+    int long_row_len;        /* SPMM_ALG_ROW_SPLIT_HYBRID: rows with more nonzeros than
+                                this are cut into warp segments; 0 selects 4 batches of
+                                the lane group (32 nonzeros for lane groups of <= 8
+                                lanes, 4 x lanes otherwise)                             */
     double merge_threshold;  /* heuristic threshold on nnz / m; <= 0 selects 9.35       */
     long long max_row_len;   /* SPMM_ALG_AUTO_GB300: longest row of A when the caller
                                 knows it; 0 makes the call measure it on the device
@@ -120,19 +131,20 @@ long long spmm_launch_count(void);
 int spmm_select_alg(int m, long long nnz, double threshold);
 
 /*
- * GB300 selector (SPMM_ALG_AUTO_GB300), pure host function.  Returns
- * SPMM_ALG_MERGE when either
- *   - the longest row is long enough to be the critical path of row split
- *     (Type 1 imbalance, Section 3.2): max_row_len > 1024 and
- *     max_row_len * 8192 > nnz (fitted on a GB300 sweep of dense-as-CSR
- *     matrices from 2 x 2^23 to 2^23 x 2), or
- *   - a row of B is at least 64 bytes (n * element size of B) and the mean
- *     row length d = nnz / m is below a threshold T: T = 7 for rows of B of
- *     256 bytes or more, T = 3 for 64-255 bytes, and 2T when the longest row is
- *     at least 2d (uneven rows); measured crossovers of the two kernels on
- *     GB300 for uniform and Poisson row lengths (the paper's single 9.35 was
- *     measured on a K40c);
- * and SPMM_ALG_ROW_SPLIT otherwise.  m == 0 returns row split.
+ * GB300 selector (SPMM_ALG_AUTO_GB300), pure host function.  When the
+ * longest row is long enough to be the critical path of row split (Type 1
+ * imbalance, Section 3.2: max_row_len > 1024 and max_row_len * 8192 > nnz,
+ * fitted on a GB300 sweep of dense-as-CSR matrices from 2 x 2^23 to
+ * 2^23 x 2) it returns SPMM_ALG_ROW_SPLIT_HYBRID for rows of B under 64
+ * bytes (n * element size of B) and SPMM_ALG_MERGE otherwise (measured on
+ * the 10^6 x 10^6 power-law matrix: the hybrid is ahead at 32-byte rows,
+ * merge from 128-byte rows on).  Otherwise it returns SPMM_ALG_MERGE when a
+ * row of B is at least 64 bytes and the mean row length d = nnz / m is below
+ * a threshold T: T = 7 for rows of B of 256 bytes or more, T = 3 for 64-255
+ * bytes, and 2T when the longest row is at least 2d (uneven rows); measured
+ * crossovers of the two kernels on GB300 for uniform and Poisson row lengths
+ * (the paper's single 9.35 was measured on a K40c); and SPMM_ALG_ROW_SPLIT
+ * otherwise.  m == 0 returns row split.
  */
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type);
 

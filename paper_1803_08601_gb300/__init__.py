@@ -21,7 +21,7 @@ import ctypes
 import os
 import threading
 
-ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300, ALG_TILED = 0, 1, 2, 3, 4
+ALG_AUTO, ALG_ROW_SPLIT, ALG_MERGE, ALG_AUTO_GB300, ALG_TILED, ALG_ROW_SPLIT_HYBRID = 0, 1, 2, 3, 4, 5
 F32, BF16, F16 = 0, 1, 2
 SEMIRING_PLUS_TIMES, SEMIRING_MIN_PLUS, SEMIRING_MAX_PLUS, SEMIRING_MAX_TIMES = 0, 1, 2, 3
 SEMIRINGS = {"plus_times": SEMIRING_PLUS_TIMES, "min_plus": SEMIRING_MIN_PLUS, "max_plus": SEMIRING_MAX_PLUS,
@@ -31,7 +31,8 @@ ERR_INVALID_VALUE, ERR_ALLOC, ERR_LAUNCH, ERR_BAD_CSR, ERR_TIMEOUT, ERR_UNSUPPOR
 PAPER_THRESHOLD = 9.35  # Section 5.4
 
 _ALG_NAMES = {"auto": ALG_AUTO, "row_split": ALG_ROW_SPLIT, "rowsplit": ALG_ROW_SPLIT, "merge": ALG_MERGE,
-              "auto_gb300": ALG_AUTO_GB300, "tiled": ALG_TILED}
+              "auto_gb300": ALG_AUTO_GB300, "tiled": ALG_TILED, "hybrid": ALG_ROW_SPLIT_HYBRID,
+              "row_split_hybrid": ALG_ROW_SPLIT_HYBRID}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspmm_gb300.so")
 _lock = threading.Lock()
@@ -48,7 +49,7 @@ class SpmmTuning(ctypes.Structure):
     """Mirror of spmm_tuning_t (zero fields = library's choice)."""
 
     _fields_ = [("lanes_per_row", ctypes.c_int), ("column_slabs", ctypes.c_int),
-                ("items_per_subwarp", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("items_per_subwarp", ctypes.c_int), ("long_row_len", ctypes.c_int),
                 ("merge_threshold", ctypes.c_double), ("max_row_len", ctypes.c_longlong)]
 
 

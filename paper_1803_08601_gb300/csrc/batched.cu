@@ -519,7 +519,11 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
         const int W = lanes_for(std::max(v[b].n, 1));
         int alg = SPMM_ALG_ROW_SPLIT, sc = 0;
         if (policy == SPMM_BATCHED_MERGE) alg = SPMM_ALG_MERGE;
-        else if (policy == SPMM_BATCHED_MODEL) alg = spmm_select_alg_gb300(v[b].m, v[b].nnz, lmax[b], v[b].n, SPMM_F32);
+        else if (policy == SPMM_BATCHED_MODEL) {
+            alg = spmm_select_alg_gb300(v[b].m, v[b].nnz, lmax[b], v[b].n, SPMM_F32);
+            // the batched kernels balance a matrix's long rows by merge tiles (no segment queue)
+            if (alg == SPMM_ALG_ROW_SPLIT_HYBRID) alg = SPMM_ALG_MERGE;
+        }
         else if (policy == SPMM_BATCHED_AUTOTUNE) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             const Choice c = g_tune_cache[bucket_of(sms, v[b])];

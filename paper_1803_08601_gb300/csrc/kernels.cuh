@@ -35,6 +35,33 @@ struct RowSplitArgs {
     long long ldc;
 };
 
+// Long rows of the hybrid row split (see rowsplit_segment_kernel): a row with
+// more than long_len nonzeros leaves the row pass.  It is cut into
+// nseg = min(ceil(len / seg_len), kMaxRowSegs) segments of equal length; each
+// segment is taken by a whole warp.  A row of one segment is queued in
+// single[]; a row of several reserves nseg consecutive partial slots, and slot
+// p holds its segment p - first in multi[p].
+constexpr int kMaxRowSegs = 64;
+
+__host__ __device__ __forceinline__ int long_row_segments(long long len, int seg_len) {
+    const long long s = (len + seg_len - 1) / seg_len;
+    return (int)(s < kMaxRowSegs ? s : kMaxRowSegs);
+}
+
+struct LongRowArgs {
+    int long_len;     // rows with more nonzeros than this are cut into segments
+    int seg_len;      // nonzeros per segment (before the kMaxRowSegs cap)
+    int max_singles;  // capacity of single[]
+    int max_parts;    // capacity of multi[], arrive[] and the rows of partial[]
+    int* counts;      // [3]: single rows queued, partial slots reserved, segment work items taken
+                      // (zeroed before the row pass)
+    int* single;      // [max_singles]: rows of one segment
+    int2* multi;      // [max_parts]: (row, first partial slot of the row) of the segment in this slot
+    int* arrive;      // [max_parts]: segments of a row finished so far, at the row's first partial slot
+    float* partial;   // [max_parts][n]: one partial sum per segment of a row with several segments
+    int* status;      // optional device status word
+};
+
 // ============================================================================ row split
 //
 // Algorithm I (Section 4.1, Fig. 3).  Sub-warp of W lanes per row; the warp's
@@ -47,8 +74,13 @@ struct RowSplitArgs {
 // do, but the lanes still join the warp's shuffles) computes the `slab`-th
 // W * VEC columns of C[row, :].  Every lane of the warp must call this the
 // same number of times.
-template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
-__device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long row, int slab) {
+//
+// With kLong (the hybrid row split), a row longer than l->long_len is not
+// computed here: the lane group of slab 0 reserves the row's segments and
+// partial slots and queues their descriptors; no lane group stores the row.
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes, bool kLong = false>
+__device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long row, int slab,
+                                             const LongRowArgs* l = nullptr) {
     constexpr int U = kUnroll;
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
     constexpr int BS = W * CV;               // nonzeros per batch
@@ -64,6 +96,37 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
     if (row < a.m) {
         rs = __ldg(a.row_ptr + row);
         re = __ldg(a.row_ptr + row + 1);
+    }
+    bool queued = false;
+    if constexpr (kLong) {
+        const int len = re - rs;
+        if (len > l->long_len) {  // the whole lane group sees the same row
+            queued = true;
+            if (slab == 0) {
+                const unsigned gmask = W == 32 ? kFullMask : (((1u << W) - 1u) << (lane & ~(W - 1)));
+                const int nseg = long_row_segments(len, l->seg_len);
+                int at = 0;
+                if (sl == 0) at = atomicAdd(nseg > 1 ? l->counts + 1 : l->counts, nseg > 1 ? nseg : 1);
+                at = __shfl_sync(gmask, at, 0, W);
+                if (nseg == 1) {
+                    if (at < l->max_singles) {
+                        if (sl == 0) l->single[at] = (int)row;
+                    } else if (sl == 0) {
+                        report(l->status, SPMM_ERR_BAD_CSR);  // more nonzeros than the workspace was sized for
+                    }
+                } else if ((long long)at + nseg <= l->max_parts) {
+                    for (int i = sl; i < nseg; i += W) l->multi[at + i] = make_int2((int)row, at);
+                    if (sl == 0) l->arrive[at] = 0;
+                } else {
+                    // more nonzeros than the workspace was sized for (nnz below row_ptr[m]): the row is
+                    // left out, and its reserved slots that exist are marked empty for the segment pass
+                    for (long long i = (long long)at + sl; i < (long long)at + nseg && i < l->max_parts; i += W)
+                        l->multi[i] = make_int2(-1, 0);
+                    if (sl == 0) report(l->status, SPMM_ERR_BAD_CSR);
+                }
+            }
+            re = rs;
+        }
     }
     float acc[VEC];
 #pragma unroll
@@ -102,7 +165,7 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
             }
         }
     }
-    if (row < a.m && col_ok) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc);
+    if (row < a.m && col_ok && !queued) store_vec<TC, VEC>(static_cast<TC*>(a.C) + row * a.ldc + col0, acc);
 }
 
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
@@ -111,6 +174,208 @@ __global__ void __launch_bounds__(kThreads) rowsplit_kernel(RowSplitArgs a) {
     const long long row =
         (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / W;
     rowsplit_row<TV, TB, TC, VEC, W, SR>(a, row, blockIdx.y);
+}
+
+// ============================================================================ hybrid row split
+//
+// Type 1 imbalance (Section 3.2): under the row split a row of L nonzeros
+// holds its lane group for L / BS batches, so with power-law row lengths a
+// few rows of 10^5 nonzeros set the time of the whole launch.  The hybrid
+// chooses the granularity of Section 4.1 per row.  Rows of at most long_len
+// nonzeros stay with their lane group (row pass: rowsplit_row with kLong);
+// longer rows are cut into segments of seg_len nonzeros, and each segment is
+// taken by a whole warp (segment pass, below).  Within a warp batch lane
+// group g owns the nonzeros at positions c * 32 + g * W + (0 .. W-1) of the
+// batch, so the warp reads col_ind / vals in whole 128-byte lines; the lane
+// groups' sums are added by xor shuffles.  A row of one segment is stored by
+// its warp.  The segments of a longer row leave their partial sums in
+// global memory; the warp that finishes the row's last segment (counted on
+// the row's arrival counter, after a device-scope fence) adds them in
+// segment order and stores the row, so the result does not depend on which
+// warp finishes last.
+
+// Row pass of the hybrid: the row split of every short row; long rows are
+// queued.  The segment pass may be scheduled as soon as every CTA has started.
+// The plain row split of 16-byte vectors with 4 or 8 lanes per row fits 40
+// registers (six CTAs per SM); the row pass is held to the same occupancy.
+template <int VEC, int W>
+__host__ __device__ constexpr int row_pass_min_blocks() { return (VEC > 1 && (W == 4 || W == 8)) ? 6 : 1; }
+
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
+__global__ void __launch_bounds__(kThreads, row_pass_min_blocks<VEC, W>()) rowsplit_hybrid_kernel(RowSplitArgs a,
+                                                                                                  LongRowArgs l) {
+    pdl_launch_dependents();
+    constexpr int RPW = 32 / W;
+    const long long row =
+        (long long)blockIdx.x * (kThreads / W) + (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / W;
+    rowsplit_row<TV, TB, TC, VEC, W, SR, true>(a, row, blockIdx.y, &l);
+}
+
+// C[row, :] = partial sums of the row's nseg segments added in segment order
+// (all n columns, by one warp), rounded once to TC.
+template <typename TC, typename SR>
+__device__ __forceinline__ void finish_long_row(const float* __restrict__ part, int nseg, int n, TC* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    if ((n & 3) == 0) {  // rows of partial[] are 16-byte aligned
+        for (int c = lane * 4; c < n; c += 128) {
+            float4 sum = make_float4(SR::identity(), SR::identity(), SR::identity(), SR::identity());
+            int t = 0;
+            for (; t + 8 <= nseg; t += 8) {  // 8 loads in flight, then the adds in segment order
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = __ldcg(reinterpret_cast<const float4*>(part + (size_t)(t + u) * n + c));
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    sum = make_float4(SR::add(sum.x, x[u].x), SR::add(sum.y, x[u].y), SR::add(sum.z, x[u].z),
+                                      SR::add(sum.w, x[u].w));
+            }
+            for (; t < nseg; ++t) {
+                const float4 x = __ldcg(reinterpret_cast<const float4*>(part + (size_t)t * n + c));
+                sum = make_float4(SR::add(sum.x, x.x), SR::add(sum.y, x.y), SR::add(sum.z, x.z), SR::add(sum.w, x.w));
+            }
+            out[c] = Elem<TC>::from_f(sum.x);
+            out[c + 1] = Elem<TC>::from_f(sum.y);
+            out[c + 2] = Elem<TC>::from_f(sum.z);
+            out[c + 3] = Elem<TC>::from_f(sum.w);
+        }
+    } else {
+        for (int c = lane; c < n; c += 32) {
+            float sum = SR::identity();
+            int t = 0;
+            for (; t + 8 <= nseg; t += 8) {
+                float x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = __ldcg(part + (size_t)(t + u) * n + c);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sum = SR::add(sum, x[u]);
+            }
+            for (; t < nseg; ++t) sum = SR::add(sum, __ldcg(part + (size_t)t * n + c));
+            out[c] = Elem<TC>::from_f(sum);
+        }
+    }
+}
+
+// Segment pass of the hybrid: persistent warps take (slab, segment) work items
+// from a counter, slab-major, so the warps running together gather from one
+// column slab of B.  The (column, value) pairs of the next warp batch are
+// loaded while the current batch's gathers are in flight.
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
+__global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitArgs a, LongRowArgs l, int slabs) {
+    constexpr int U = kUnroll;
+    constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per warp batch
+    constexpr int BS = W * CV;               // nonzeros per lane group per warp batch
+    constexpr int G = BS / U;                // groups of U gathers per batch
+    constexpr int WB = 32 * CV;              // nonzeros per warp batch
+    pdl_wait();  // the row pass has queued every segment
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (W - 1);
+    const int grp = lane / W;
+    const TV* __restrict__ vals = static_cast<const TV*>(a.vals);
+    const TB* __restrict__ B = static_cast<const TB*>(a.B);
+    TC* __restrict__ C = static_cast<TC*>(a.C);
+    // segments of rows with several first (the longest rows start earliest), then the single rows
+    const int n_multi = min(__ldcg(l.counts + 1), l.max_parts);
+    const int n_single = min(__ldcg(l.counts), l.max_singles);
+    const int count = n_multi + n_single;
+    const long long items = (long long)count * slabs;
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(reinterpret_cast<unsigned int*>(l.counts + 2), 1u);
+        item = __shfl_sync(kFullMask, item, 0);
+        if (item >= items) break;
+        const int slab = (int)(item / count);
+        const int i = (int)(item - (long long)slab * count);
+        const long long col0 = (long long)slab * (W * VEC) + (long long)sl * VEC;
+        const bool col_ok = col0 < a.n;
+        int row, pfirst = -1;
+        if (i < n_multi) {
+            const int2 d = __ldcg(l.multi + i);
+            row = d.x;
+            pfirst = d.y;
+        } else {
+            row = __ldcg(l.single + (i - n_multi));
+        }
+        if (row < 0 || row >= a.m) continue;  // a slot of a reservation that did not fit
+        const int rs = __ldg(a.row_ptr + row), re = __ldg(a.row_ptr + row + 1);
+        const int nseg = pfirst < 0 ? 1 : long_row_segments(re - rs, l.seg_len);
+        const int len_s = (re - rs + nseg - 1) / nseg;  // nonzeros per segment of this row
+        const int p0 = pfirst < 0 ? rs : rs + (i - pfirst) * len_s;
+        const int p1 = (int)min((long long)p0 + len_s, (long long)re);
+        float acc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = SR::identity();
+        int mc[CV];
+        float mv[CV];
+#pragma unroll
+        for (int c = 0; c < CV; ++c) {
+            const int p = p0 + c * 32 + lane;
+            const bool ok = p < p1;
+            mc[c] = ok ? __ldg(a.col_ind + p) : 0;
+            mv[c] = ok ? load_f(vals + p) : 0.0f;
+        }
+        for (int base = p0; base < p1; base += WB) {
+            int nc[CV];
+            float nv[CV];
+#pragma unroll
+            for (int c = 0; c < CV; ++c) {
+                const int p = base + WB + c * 32 + lane;
+                const bool ok = p < p1;
+                nc[c] = ok ? __ldg(a.col_ind + p) : 0;
+                nv[c] = ok ? load_f(vals + p) : 0.0f;
+            }
+            // this lane group's nonzero j of the batch sits at base + grp * W + (j / W) * 32 + j % W,
+            // so it exists iff (j / W) * 32 + j % W < lim
+            const int lim = p1 - base - grp * W;
+            auto in = [&](int j) { return (j / W) * 32 + (j % W) < lim; };
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (g > 0 && __all_sync(kFullMask, !in(g * U))) break;
+                Raw<TB, VEC> bv[U];
+                float vv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = g * U + u;
+                    const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
+                    vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
+                    bv[u] = (in(j) && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0)
+                                              : zero_raw<TB, VEC>();
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if constexpr (SR::kZeroPadOk) fma_raw<TB, VEC>(acc, vv[u], bv[u]);
+                    else if (in(g * U + u)) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CV; ++c) {
+                mc[c] = nc[c];
+                mv[c] = nv[c];
+            }
+        }
+#pragma unroll
+        for (int off = W; off < 32; off <<= 1)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[e] = SR::add(acc[e], __shfl_xor_sync(kFullMask, acc[e], off));
+        if (nseg == 1) {
+            if (grp == 0 && col_ok) store_vec<TC, VEC>(C + (long long)row * a.ldc + col0, acc);
+            continue;
+        }
+        const int slot = i;
+        if (grp == 0 && col_ok) {
+            float* pp = l.partial + (size_t)slot * a.n + col0;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) pp[e] = acc[e];
+        }
+        __threadfence();  // this lane's partial is visible device-wide before the arrival below
+        __syncwarp();
+        int prev = 0;
+        if (lane == 0) prev = atomicAdd(l.arrive + pfirst, 1);
+        prev = __shfl_sync(kFullMask, prev, 0);
+        if ((long long)prev == (long long)nseg * slabs - 1) {  // every segment of every slab is in
+            __threadfence();
+            finish_long_row<TC, SR>(l.partial + (size_t)pfirst * a.n, nseg, a.n, C + (long long)row * a.ldc);
+        }
+    }
 }
 
 // ============================================================================ merge path

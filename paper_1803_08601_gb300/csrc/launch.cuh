@@ -29,6 +29,7 @@ using FixupFn = cudaError_t (*)(const MergeArgs&, cudaStream_t);
 using SpmvRowSplitFn = cudaError_t (*)(const RowSplitArgs&, int lanes, cudaStream_t);
 using SpmvMergeFn = cudaError_t (*)(const MergeArgs&, int items_per_thread, cudaStream_t);
 using TiledFn = cudaError_t (*)(const TiledArgs&, const Shape&, cudaStream_t);
+using RowSplitHybridFn = cudaError_t (*)(const RowSplitArgs&, const LongRowArgs&, const Shape&, int sms, cudaStream_t);
 
 struct Launchers {
     RowSplitFn rowsplit;
@@ -38,6 +39,7 @@ struct Launchers {
     SpmvRowSplitFn spmv_rowsplit;  // n = 1
     SpmvMergeFn spmv_merge;        // n = 1, tiles of kThreads * items_per_thread items (4, 8 or 16)
     TiledFn tiled;                 // A/B tiling; 16-byte vectors only (shape.vec > 1)
+    RowSplitHybridFn rowsplit_hybrid;  // row pass + segment pass of the hybrid row split
 };
 
 // defined in inst_*.cu
@@ -81,6 +83,72 @@ template <typename TV, typename TB, typename TC, typename SR>
 cudaError_t rowsplit_launch(const RowSplitArgs& a, const Shape& s, cudaStream_t st) {
     constexpr int V = Elem<TB>::kVec;
     return s.vec == 1 ? rowsplit_launch_vec<TV, TB, TC, 1, SR>(a, s, st) : rowsplit_launch_vec<TV, TB, TC, V, SR>(a, s, st);
+}
+
+// Hybrid row split: zero the queue counters, then the row pass (grid as the
+// plain row split) and the segment pass, a persistent grid of one wave chained
+// behind the row pass with programmatic dependent launch.
+template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
+cudaError_t hybrid_launch_one(const RowSplitArgs& a, const LongRowArgs& l, const Shape& s, int sms, cudaStream_t st) {
+    const long long rows_per_cta = kThreads / W;
+    const long long gx = (a.m + rows_per_cta - 1) / rows_per_cta;
+    if (gx > 0x7fffffffLL || s.slabs > 65535 || s.slabs < 1) return cudaErrorInvalidConfiguration;
+    auto seg_kern = rowsplit_segment_kernel<TV, TB, TC, VEC, W, SR>;
+    static thread_local int cached_dev = -1;
+    static thread_local int cached_blocks = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != cached_dev) {
+        int blocks = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, seg_kern, kThreads, 0);
+        if (e != cudaSuccess) return e;
+        cached_dev = dev;
+        cached_blocks = blocks < 1 ? 1 : blocks;
+    }
+    e = cudaMemsetAsync(l.counts, 0, 3 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    rowsplit_hybrid_kernel<TV, TB, TC, VEC, W, SR><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a, l);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const long long warps_per_cta = kThreads / 32;
+    long long sx = (long long)cached_blocks * std::max(sms, 1);
+    sx = std::min<long long>(sx, ((long long)(l.max_singles + l.max_parts) * s.slabs + warps_per_cta - 1) / warps_per_cta);
+    if (sx < 1) sx = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)sx);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, seg_kern, a, l, s.slabs);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+template <typename TV, typename TB, typename TC, int VEC, typename SR>
+cudaError_t hybrid_launch_vec(const RowSplitArgs& a, const LongRowArgs& l, const Shape& s, int sms, cudaStream_t st) {
+    switch (s.W) {
+        case 1: return hybrid_launch_one<TV, TB, TC, VEC, 1, SR>(a, l, s, sms, st);
+        case 2: return hybrid_launch_one<TV, TB, TC, VEC, 2, SR>(a, l, s, sms, st);
+        case 4: return hybrid_launch_one<TV, TB, TC, VEC, 4, SR>(a, l, s, sms, st);
+        case 8: return hybrid_launch_one<TV, TB, TC, VEC, 8, SR>(a, l, s, sms, st);
+        case 16: return hybrid_launch_one<TV, TB, TC, VEC, 16, SR>(a, l, s, sms, st);
+        case 32: return hybrid_launch_one<TV, TB, TC, VEC, 32, SR>(a, l, s, sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TV, typename TB, typename TC, typename SR>
+cudaError_t hybrid_launch(const RowSplitArgs& a, const LongRowArgs& l, const Shape& s, int sms, cudaStream_t st) {
+    constexpr int V = Elem<TB>::kVec;
+    return s.vec == 1 ? hybrid_launch_vec<TV, TB, TC, 1, SR>(a, l, s, sms, st)
+                      : hybrid_launch_vec<TV, TB, TC, V, SR>(a, l, s, sms, st);
 }
 
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
@@ -280,7 +348,7 @@ template <typename TV, typename TB, typename TC, typename SR = PlusTimes>
 Launchers make_launchers() {
     return Launchers{&rowsplit_launch<TV, TB, TC, SR>, &merge_launch<TV, TB, TC, SR>, &merge_smem<TV, TB, TC>,
                      &fixup_launch<TC, SR>, &spmv_rowsplit_launch<TV, TB, TC, SR>, &spmv_merge_launch<TV, TB, TC, SR>,
-                     &tiled_launch<TV, TB, TC, SR>};
+                     &tiled_launch<TV, TB, TC, SR>, &hybrid_launch<TV, TB, TC, SR>};
 }
 
 }  // namespace spmm

@@ -123,8 +123,11 @@ __global__ void rebase_kernel(int* __restrict__ row_ptr, int count, int base) {
     if (i < count) row_ptr[i] -= base;
 }
 
-// Longest row by a grid-stride max reduction over row_ptr differences.
+// Longest row by a grid-stride max reduction over row_ptr differences into
+// out[0] (zeroed before the launch); the first thread also copies
+// row_ptr[m] (= nnz) to out[1].
 __global__ void row_length_max_kernel(const int* __restrict__ row_ptr, int m, int* __restrict__ out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[1] = __ldg(row_ptr + m);
     int best = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
         best = max(best, __ldg(row_ptr + i + 1) - __ldg(row_ptr + i));
@@ -172,13 +175,16 @@ bool choose_shape(int n, int tb, int tc, const void* B, long long ldb, const voi
 // L2 (measured on GB300: merge with 512-byte rows and row split with >= 256-byte
 // rows of a B beyond L2 gain 6-14 %; narrower rows lose).
 int default_slabs(int alg, int k, int n, int b_type) {
-    static int l2_bytes[64] = {};
+    static std::atomic<int> l2_cache[64];  // 0 until first queried; every thread stores the same value
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (l2_bytes[dev] == 0 && cudaDeviceGetAttribute(&l2_bytes[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess)
-        return 1;
+    int l2 = l2_cache[dev].load(std::memory_order_relaxed);
+    if (l2 == 0) {
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return 1;
+        l2_cache[dev].store(l2, std::memory_order_relaxed);
+    }
     const long long row_bytes = (long long)n * dtype_size(b_type);
-    if ((long long)k * row_bytes <= 2LL * l2_bytes[dev]) return 1;
+    if ((long long)k * row_bytes <= 2LL * l2) return 1;
     const long long min_row = alg == SPMM_ALG_MERGE ? 512 : 256;
     return row_bytes >= min_row ? 2 : 1;
 }
@@ -211,6 +217,42 @@ MergeLayout merge_layout_items(int m, long long nnz, int n, long long ipt) {
 
 MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
     return merge_layout_items(m, nnz, n, (long long)(merge_cta_threads(s.W) / s.W) * s.ips);
+}
+
+// Hybrid row split (SPMM_ALG_ROW_SPLIT_HYBRID).  A lane group of W lanes
+// takes BS = max(W, kUnroll) nonzeros per batch; a row stays in the row pass
+// for at most 4 batches (long_len = 4 BS unless the caller sets it), and a
+// segment holds 16 warp batches (32 / W lane groups x BS nonzeros each).
+struct HybridLayout {
+    int long_len, seg_len, max_singles, max_parts;
+    size_t off_counts, off_single, off_multi, off_arrive, off_partial, total;
+};
+
+HybridLayout hybrid_layout(long long nnz, int n, const Shape& s, int long_len_req) {
+    HybridLayout H{};
+    const int bs = std::max(s.W, kUnroll);
+    H.long_len = long_len_req > 0 ? long_len_req : 4 * bs;
+    H.seg_len = 16 * (32 / s.W) * bs;
+    // single rows: at most nnz / (long_len + 1) rows are longer than long_len; partial slots: a row of
+    // L > seg_len nonzeros takes at most ceil(L / seg_len) <= L / seg_len + 1 of them, and there are at
+    // most nnz / (seg_len + 1) such rows
+    const long long singles = nnz / ((long long)H.long_len + 1) + 1;
+    const long long parts = 2 * (nnz / H.seg_len) + 2;
+    H.max_singles = (int)std::min<long long>(singles, 0x7fffffffLL);
+    H.max_parts = (int)std::min<long long>(parts, 0x7fffffffLL);
+    size_t off = 0;
+    H.off_counts = off;
+    off = align256(off + 3 * sizeof(int));
+    H.off_single = off;
+    off = align256(off + (size_t)H.max_singles * sizeof(int));
+    H.off_multi = off;
+    off = align256(off + (size_t)H.max_parts * sizeof(int2));
+    H.off_arrive = off;
+    off = align256(off + (size_t)H.max_parts * sizeof(int));
+    H.off_partial = off;
+    off = align256(off + (size_t)H.max_parts * (size_t)n * sizeof(float));
+    H.total = off;
+    return H;
 }
 
 // Lanes per row of the SpMV row split: the power of two at or below a sixth
@@ -328,7 +370,7 @@ int cuda_status(cudaError_t e) {
 int check_args(int m, int k, int n, long long nnz, const int* row_ptr, const int* col_ind, const void* vals,
                const void* B, long long ldb, const void* C, long long ldc, int alg) {
     if (m < 0 || k < 0 || n < 0 || nnz < -1 || nnz > 0x7fffffffLL) return SPMM_ERR_INVALID_VALUE;
-    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_TILED) return SPMM_ERR_INVALID_VALUE;
+    if (alg < SPMM_ALG_AUTO || alg > SPMM_ALG_ROW_SPLIT_HYBRID) return SPMM_ERR_INVALID_VALUE;
     if (m > 0 && n > 0) {
         if (!row_ptr || !C) return SPMM_ERR_INVALID_VALUE;
         if (ldc < n) return SPMM_ERR_INVALID_VALUE;
@@ -336,6 +378,38 @@ int check_args(int m, int k, int n, long long nnz, const int* row_ptr, const int
         if (nnz != 0 && k > 0 && (!B || ldb < n)) return SPMM_ERR_INVALID_VALUE;
         if (nnz > 0 && k == 0) return SPMM_ERR_INVALID_VALUE;  // a nonzero needs a column
     }
+    return SPMM_OK;
+}
+
+// Longest row of A and, when nnz is not NULL, nnz = row_ptr[m], in one launch
+// and one synchronisation of st.  The two result words live in a device
+// buffer per host thread and device, allocated on first use and kept until
+// exit; the call synchronises st before it returns, so no two calls have the
+// same words in flight.
+int probe_rows(const int* row_ptr, int m, cudaStream_t st, long long* lmax, long long* nnz) {
+    static thread_local int* words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SPMM_ERR_CUDA;
+    if (!words[dev] && cudaMalloc(&words[dev], 2 * sizeof(int)) != cudaSuccess) {
+        words[dev] = nullptr;
+        return SPMM_ERR_ALLOC;
+    }
+    int* d = words[dev];
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    const int threads = 256;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)m + threads - 1) / threads, 4 * 152));
+    if (e == cudaSuccess) {
+        row_length_max_kernel<<<blocks, threads, 0, st>>>(row_ptr, m, d);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h[1] < 0) return SPMM_ERR_BAD_CSR;
+    *lmax = h[0];
+    if (nnz) *nnz = h[1];
     return SPMM_OK;
 }
 
@@ -363,19 +437,16 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     if (!L) return SPMM_ERR_UNSUPPORTED;
     if (m == 0 || n == 0) return SPMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (nnz < 0) {
+    long long lmax = tuning ? tuning->max_row_len : 0;
+    if (alg == SPMM_ALG_AUTO_GB300 && lmax <= 0) {  // longest row (and nnz if unknown): one synchronisation
+        st = probe_rows(row_ptr, m, s, &lmax, nnz < 0 ? &nnz : nullptr);
+        if (st != SPMM_OK) return st;
+    } else if (nnz < 0) {
         st = read_nnz(row_ptr, m, s, &nnz);
         if (st != SPMM_OK) return st;
     }
     Shape shape;
-    if (alg == SPMM_ALG_AUTO_GB300) {
-        long long lmax = tuning ? tuning->max_row_len : 0;
-        if (lmax <= 0) {
-            st = spmm_csr_max_row_length(m, row_ptr, &lmax, stream);
-            if (st != SPMM_OK) return st;
-        }
-        alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
-    }
+    if (alg == SPMM_ALG_AUTO_GB300) alg = spmm_select_alg_gb300(m, nnz, lmax, n, b_type);
     const int a = resolve_alg(alg, m, nnz, tuning);
     spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
     if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
@@ -384,6 +455,39 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     if (a == SPMM_ALG_TILED && shape.vec > 1 && !spmv) {
         TiledArgs ta{m, n, k, row_ptr, col_ind, vals, B, ldb, C, ldc, d_status};
         return cuda_status(L->tiled(ta, shape, s));
+    }
+    if (a == SPMM_ALG_ROW_SPLIT_HYBRID) {
+        const HybridLayout H = hybrid_layout(nnz, n, shape, t_eff.long_row_len);
+        bool own = false;
+        unsigned char* ws = static_cast<unsigned char*>(workspace);
+        if (!ws) {
+            if (workspace_bytes != 0) return SPMM_ERR_WORKSPACE;
+            void* p = nullptr;
+            keep_pool_memory();
+            if (cudaMallocAsync(&p, H.total, s) != cudaSuccess) return SPMM_ERR_ALLOC;
+            ws = static_cast<unsigned char*>(p);
+            own = true;
+        } else if (workspace_bytes < H.total || ((uintptr_t)ws % 256) != 0) {
+            return SPMM_ERR_WORKSPACE;
+        }
+        RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
+        LongRowArgs la{};
+        la.long_len = H.long_len;
+        la.seg_len = H.seg_len;
+        la.max_singles = H.max_singles;
+        la.max_parts = H.max_parts;
+        la.counts = reinterpret_cast<int*>(ws + H.off_counts);
+        la.single = reinterpret_cast<int*>(ws + H.off_single);
+        la.multi = reinterpret_cast<int2*>(ws + H.off_multi);
+        la.arrive = reinterpret_cast<int*>(ws + H.off_arrive);
+        la.partial = reinterpret_cast<float*>(ws + H.off_partial);
+        la.status = d_status;
+        st = cuda_status(L->rowsplit_hybrid(ra, la, shape, sm_count(), s));
+        if (own) {
+            const cudaError_t e = cudaFreeAsync(ws, s);
+            if (st == SPMM_OK && e != cudaSuccess) st = cuda_status(e);
+        }
+        return st;
     }
     if (a == SPMM_ALG_ROW_SPLIT || a == SPMM_ALG_TILED) {  // tiling without 16-byte access: row split
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
@@ -484,9 +588,10 @@ int spmm_select_alg(int m, long long nnz, double threshold) {
 
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type) {
     if (m <= 0) return SPMM_ALG_ROW_SPLIT;
-    if (max_row_len > 1024 && max_row_len * 8192 > nnz) return SPMM_ALG_MERGE;  // Type 1 guard
-    const double d = (double)nnz / (double)m;
     const long long row_bytes = (long long)n * (dtype_size(b_type) ? dtype_size(b_type) : 4);
+    if (max_row_len > 1024 && max_row_len * 8192 > nnz)  // Type 1 guard
+        return row_bytes < 64 ? SPMM_ALG_ROW_SPLIT_HYBRID : SPMM_ALG_MERGE;
+    const double d = (double)nnz / (double)m;
     if (row_bytes < 64) return SPMM_ALG_ROW_SPLIT;
     // mean-length crossover measured on GB300 (uniform and Poisson rows, 1M x 1M): about 7 nonzeros
     // per row for rows of B of 256 bytes or more, 3 below; about twice that when the longest row is
@@ -508,32 +613,30 @@ int spmm_csr_max_row_length(int m, const int* row_ptr, long long* max_row_len, v
     if (m < 0 || !max_row_len || (m > 0 && !row_ptr)) return SPMM_ERR_INVALID_VALUE;
     *max_row_len = 0;
     if (m == 0) return SPMM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, sizeof(int), s) != cudaSuccess) return SPMM_ERR_ALLOC;
-    int* d = static_cast<int*>(p);
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
-    const int threads = 256;
-    const int blocks = (int)std::min<long long>(((long long)m + threads - 1) / threads, 4 * 152);
-    if (e == cudaSuccess) {
-        row_length_max_kernel<<<blocks, threads, 0, s>>>(row_ptr, m, d);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
-    }
-    int v = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, s);
-    const cudaError_t ef = cudaFreeAsync(d, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = ef;
-    if (e != cudaSuccess) return cuda_status(e);
-    *max_row_len = v;
-    return SPMM_OK;
+    return probe_rows(row_ptr, m, (cudaStream_t)stream, max_row_len, nullptr);
 }
 
 size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int b_type, const spmm_tuning_t* tuning) {
     if (m < 0 || k < 0 || n < 0 || nnz < 0 || dtype_size(b_type) == 0) return 0;
-    if (alg == SPMM_ALG_AUTO_GB300) alg = SPMM_ALG_MERGE;  // the choice may need the longest row: size for merge
+    if (alg == SPMM_ALG_AUTO_GB300)  // the choice may need the longest row: size for merge and the hybrid
+        return std::max(spmm_csr_workspace_size(m, k, n, nnz, SPMM_ALG_MERGE, b_type, tuning),
+                        spmm_csr_workspace_size(m, k, n, nnz, SPMM_ALG_ROW_SPLIT_HYBRID, b_type, tuning));
     if (alg == SPMM_ALG_TILED) return 0;
+    if (alg == SPMM_ALG_ROW_SPLIT_HYBRID) {
+        if (m == 0 || n == 0) return 0;
+        size_t best = 0;
+        for (int vec : {1, 16 / dtype_size(b_type)}) {
+            for (int slabs : {0, 2}) {
+                spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
+                if (slabs && (t.column_slabs > 0 || t.lanes_per_row > 0)) continue;
+                if (slabs) t.column_slabs = slabs;
+                Shape s;
+                if (!shape_for(n, vec, &t, &s)) return 0;
+                best = std::max(best, hybrid_layout(nnz, n, s, t.long_row_len).total);
+            }
+        }
+        return best;
+    }
     if (resolve_alg(alg, m, nnz, tuning) != SPMM_ALG_MERGE || m == 0 || n == 0) return 0;
     // the access width depends on pointer alignment and the default slab count on the device's L2,
     // neither known here: size for every combination
@@ -664,7 +767,7 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
     }
     // one merge workspace, lent to every block's call in turn (they run in order on `stream`)
     size_t ws_need = 0;
-    if (alg == SPMM_ALG_MERGE)
+    if (alg == SPMM_ALG_MERGE || alg == SPMM_ALG_ROW_SPLIT_HYBRID)
         for (int c = 0; c < chunks; ++c)
             for (int j = 0; j < slabs; ++j) {
                 const long long cw = std::min<long long>(w, n - j * w);

@@ -57,7 +57,7 @@ def errors(got, rp, ci, v, B, v_r, B_r, rows=None, out="f32"):
 
 
 @pytest.mark.parametrize("combo", COMBOS)
-@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("alg", ["row_split", "merge", "hybrid"])
 @pytest.mark.parametrize("name,n", [("power_law", 64), ("giant_row", 128), ("short_rows", 8), ("uniform16", 24),
                                     ("duplicates_unsorted", 13)])
 def test_precision_forms(gpu_lib, combo, alg, name, n):

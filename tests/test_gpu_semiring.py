@@ -41,7 +41,7 @@ def expect_exact(C, rp, ci, v, B, semiring):
 
 
 @pytest.mark.parametrize("name", STRUCTURES)
-@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("alg", ["row_split", "merge", "hybrid"])
 @pytest.mark.parametrize("semiring", SEMIRINGS)
 @pytest.mark.parametrize("n", [1, 8, 13, 128])
 def test_structures_bitwise(gpu_lib, name, alg, semiring, n):
@@ -64,7 +64,7 @@ def test_selectors(gpu_lib, semiring, alg):
 
 
 @pytest.mark.parametrize("semiring", SEMIRINGS)
-@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("alg", ["row_split", "merge", "hybrid"])
 @pytest.mark.parametrize("tuning", [dict(lanes_per_row=1), dict(lanes_per_row=32), dict(column_slabs=4),
                                     dict(items_per_subwarp=4), dict(items_per_subwarp=37),
                                     dict(items_per_subwarp=700), dict(lanes_per_row=2, items_per_subwarp=5)])
@@ -98,7 +98,7 @@ def test_empty_rows_give_the_identity(gpu_lib):
     B = gen.normal_matrix(k, 32, 5)
     empty = np.diff(rp) == 0
     for semiring, ident in (("min_plus", np.inf), ("max_plus", -np.inf), ("max_times", -np.inf)):
-        for alg in ("row_split", "merge"):
+        for alg in ("row_split", "merge", "hybrid"):
             C = run(gpu_lib, torch, rp, ci, v, B, semiring, alg)
             assert np.all(C[empty] == ident)
             assert np.all(np.isfinite(C[~empty]))

@@ -9,7 +9,7 @@ from spmm_cases import FP32_TOL, STRUCTURES, check, csr_arrays, structure
 
 pytestmark = pytest.mark.gpu
 
-ALGS = ["row_split", "merge", "auto", "auto_gb300"]
+ALGS = ["row_split", "merge", "hybrid", "auto", "auto_gb300"]
 
 
 def to_dev(torch, *arrays):
@@ -37,7 +37,7 @@ def test_structures(gpu_lib, name, alg, n):
     check(C.cpu().numpy(), rp, ci, v, B)
 
 
-@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("alg", ["row_split", "merge", "hybrid"])
 @pytest.mark.parametrize("n", [4, 32, 64, 96, 256])
 def test_exact_integer_arithmetic_is_bitwise(gpu_lib, alg, n):
     """Integer vals in [-2, 2] and B in [-4, 4] with rows of up to 10^4 terms: every
@@ -66,7 +66,7 @@ def test_identity_and_permutation_are_exact(gpu_lib):
             assert np.array_equal(C, B[ci])
 
 
-@pytest.mark.parametrize("alg", ["row_split", "merge"])
+@pytest.mark.parametrize("alg", ["row_split", "merge", "hybrid"])
 @pytest.mark.parametrize("tuning", [dict(lanes_per_row=4), dict(lanes_per_row=32), dict(column_slabs=4),
                                     dict(column_slabs=2, items_per_subwarp=9), dict(items_per_subwarp=4),
                                     dict(items_per_subwarp=700), dict(lanes_per_row=1, items_per_subwarp=5)])
@@ -416,3 +416,60 @@ def test_host_entry_few_long_rows(gpu_lib):
         C = torch.empty((4, 16)).pin_memory()
         pkg.spmm_host(torch.from_numpy(rp), torch.from_numpy(ci), torch.from_numpy(v), torch.from_numpy(B), C, alg=alg)
         check(C.numpy(), rp, ci, v, B)
+
+
+@pytest.mark.parametrize("n", [1, 8, 32, 64, 128, 300])
+@pytest.mark.parametrize("long_row_len", [1, 7, 64, 1000])
+def test_hybrid_integer_rows_across_the_threshold_are_bitwise(gpu_lib, n, long_row_len):
+    """Hybrid row split: rows just below, at and above the long-row threshold and
+    rows of many segments (up to 40,000 nonzeros, so with 512-nonzero segments
+    up to 79 partial sums added by the row's last warp) on integer data: every
+    partial sum is an exact integer, so the result must equal the oracle bit
+    for bit whichever rows the row pass keeps."""
+    import torch
+
+    rng = np.random.default_rng(100 + n)
+    lens = rng.integers(0, 80, 6000)
+    lens[::211] = long_row_len
+    lens[1::211] = long_row_len + 1
+    lens[::997] = 40_000
+    lens[5] = 0
+    rp, ci, v = csr_arrays(lens, 50_000, 21, int_vals=True)
+    B = rng.integers(-4, 5, size=(50_000, n)).astype(np.float32)
+    ref = oracle.spmm(rp, ci, v, B).astype(np.float32)
+    for tuning in (dict(long_row_len=long_row_len), dict(long_row_len=long_row_len, column_slabs=3),
+                   dict(long_row_len=long_row_len, lanes_per_row=1)):
+        C = run(gpu_lib, torch, rp, ci, v, B, "hybrid", tuning=tuning)
+        assert np.array_equal(C.cpu().numpy(), ref), tuning
+
+
+def test_hybrid_is_deterministic_and_reuses_its_workspace(gpu_lib):
+    """The partial sums of a row are added in segment order by whichever warp
+    finishes last: two runs through one caller workspace give the same bits,
+    and the second run is not disturbed by the first run's queue and counters."""
+    import torch
+
+    rp, ci, v, k = structure("giant_row")
+    B = gen.normal_matrix(k, 64, 9)
+    nnz = int(rp[-1])
+    ws_bytes = gpu_lib.workspace_size(len(rp) - 1, k, 64, nnz, alg="hybrid")
+    assert ws_bytes > 0
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    ws.fill_(0xA5)  # stale contents must not matter
+    outs = []
+    for _ in range(3):
+        C = run(gpu_lib, torch, rp, ci, v, B, "hybrid", workspace=ws)
+        outs.append(C.cpu().numpy())
+    check(outs[0], rp, ci, v, B)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_hybrid_rejects_a_short_workspace(gpu_lib):
+    import torch
+
+    rp, ci, v, k = structure("power_law")
+    B = gen.normal_matrix(k, 32, 1)
+    need = gpu_lib.workspace_size(len(rp) - 1, k, 32, int(rp[-1]), alg="hybrid")
+    ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gpu_lib.SpMMError):
+        run(gpu_lib, torch, rp, ci, v, B, "hybrid", workspace=ws)

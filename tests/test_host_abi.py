@@ -54,8 +54,12 @@ def test_heuristic_matches_oracle(lib, m, nnz):
 
 def test_gb300_selector(lib):
     F, H = pkg.F32, pkg.BF16
-    # Type 1 guard: a very long row sends a matrix with a long mean row length to merge
+    # Type 1 guard: a very long row sends a matrix with a long mean row length to merge, or to the
+    # hybrid row split when rows of B are under 64 bytes
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 64, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 32, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 8, F) == pkg.ALG_ROW_SPLIT_HYBRID
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 16, H) == pkg.ALG_ROW_SPLIT_HYBRID
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 1_000, 64, F) == pkg.ALG_ROW_SPLIT
     assert pkg.spmm_select_alg_gb300(4096, 65_536, 16, 64, F) == pkg.ALG_ROW_SPLIT
     # the aspect-ratio sweep's boundary: 4096 rows of 4096 go to merge, 8192 rows of 2048 to row split
@@ -100,7 +104,7 @@ def test_argument_checks_return_before_any_device_work(lib):
     assert call(ldb=3) == pkg.ERR_INVALID_VALUE
     assert call(ldc=2) == pkg.ERR_INVALID_VALUE
     assert call(alg=7) == pkg.ERR_INVALID_VALUE
-    assert call(alg=5) == pkg.ERR_INVALID_VALUE
+    assert call(alg=6) == pkg.ERR_INVALID_VALUE
     assert call(alg=pkg.ALG_TILED, m=0) == pkg.OK
     assert call(row_ptr=None) == pkg.ERR_INVALID_VALUE
     assert call(C=None) == pkg.ERR_INVALID_VALUE
@@ -199,3 +203,22 @@ def test_tiled_needs_no_workspace_and_reuse_formula(lib):
     assert abs(pkg.spmm_tiled_reuse(1000, 1000, 1000, 64, pkg.BF16) - 256 * 1e-3) < 1e-12
     assert pkg.spmm_tiled_reuse(0, 10, 0, 64, pkg.F32) == 0.0
 
+
+
+def test_hybrid_workspace_size(lib):
+    """The hybrid row split's queue and partial sums are sized from nnz and n on
+    the host: nothing for an empty product, more for wider B and for a lower
+    long-row threshold (more rows may be queued)."""
+    F = pkg.F32
+    H = pkg.ALG_ROW_SPLIT_HYBRID
+    assert pkg.spmm_csr_workspace_size(0, 10, 8, 0, H, F) == 0
+    assert pkg.spmm_csr_workspace_size(10, 10, 0, 0, H, F) == 0
+    w8 = pkg.spmm_csr_workspace_size(1_000_000, 1_000_000, 8, 15_821_532, H, F)
+    w128 = pkg.spmm_csr_workspace_size(1_000_000, 1_000_000, 128, 15_821_532, H, F)
+    assert 0 < w8 < w128
+    t = pkg.SpmmTuning(long_row_len=1)
+    low = pkg.spmm_csr_workspace_size(1_000_000, 1_000_000, 8, 15_821_532, H, F, t)
+    assert low > w8
+    # every queued row needs a 4-byte entry: with rows of 2 nonzeros and a threshold of 1, all 10^6
+    # rows may be queued
+    assert pkg.spmm_csr_workspace_size(1_000_000, 1_000_000, 8, 2_000_000, H, F, t) >= 4 * 1_000_000
