@@ -67,11 +67,12 @@ def parse():
     p.add_argument("--ingest-ncu", default=None, metavar="CSV",
                    help="instead of the benchmark: turn the ncu CSV of the traffic capture (the command recorded in "
                         "profiles/merge_kernel_power_law_1M_dram.json, with --print-units base) into that JSON")
-    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv", "tiling", "selector"],
+    p.add_argument("--sweep", default=None, choices=["aspect", "density", "spmv", "tiling", "selector", "gather"],
                    help="instead of the benchmark: the aspect-ratio sweep (dense-as-CSR m x k with m*k = 2^24, "
                         "n = 64), the density sweep against dense GEMM (100k x 100k, n = 64) or SpMV (n = 1) on "
                         "five matrices against cuSPARSE through torch, the A/B tiling against both families "
-                        "with B larger than L2, or both selectors over row-length families (selector); "
+                        "with B larger than L2, both selectors over row-length families (selector), or the "
+                        "gather-only probe over B sizes 16 MB - 1 GB and row widths 32-512 B (gather); "
                         "JSON line per point")
     return p.parse_args()
 
@@ -121,11 +122,44 @@ def compulsory_bytes(m, nnz, k, n, s_v=4, s_b=4, s_c=4):
     return (m + 1) * 4 + nnz * (4 + s_v) + k * n * s_b + m * n * s_c
 
 
+# Sampled GPU results kept on the host by the headline and the forms, checked against the FP64
+# oracle by the cpu_baseline leg at the end of the run (the one place besides --impl reference where
+# bench.py runs the oracle).  Each entry: (rows, row_ptr, col_ind, vals, B, C_rows, what it is).
+SAMPLES = {}
+
+
+def sample_rows(m, count, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(m, size=min(m, count), replace=False))
+
+
+def row_nonzeros(rows, row_ptr):
+    """Positions of the nonzeros of `rows` (in row order)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    parts = [np.arange(row_ptr[r], row_ptr[r + 1], dtype=np.int64) for r in rows]
+    return np.concatenate(parts) if parts else np.zeros(0, np.int64)
+
+
+def subproblem(rows, row_ptr, col_ind, vals, B):
+    """The rows `rows` of A as a CSR of their own, with the columns they touch renumbered
+    0..u-1 and B reduced to those u rows: the product of the pieces is C[rows]."""
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = (row_ptr[rows + 1] - row_ptr[rows]).astype(np.int64)
+    rp = np.zeros(len(rows) + 1, dtype=np.int32)
+    np.cumsum(lens, out=rp[1:])
+    idx = row_nonzeros(rows, row_ptr)
+    cols = col_ind[idx]
+    uniq, ci = np.unique(cols, return_inverse=True)
+    return rp, ci.astype(np.int32), np.ascontiguousarray(vals[idx]), np.ascontiguousarray(B[uniq])
+
+
+GATHER_JSON = os.path.join(ROOT, "profiles", "gather_ceiling_sweep.jsonl")
 TRAFFIC_SOURCES = ["paper_1803_08601_gb300/csrc/kernels.cuh", "paper_1803_08601_gb300/csrc/common.cuh"]
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "merge_kernel_power_law_1M_dram.json")
 TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_sector_hit_rate.pct,"
                    "gpu__time_duration.sum --print-units base --clock-control none -k regex:merge_kernel -s 12 -c 4 "
-                   "--csv --log-file <CSV> python bench.py --steps 1 --warmup 3 --no-extras --forms= --no-clocks")
+                   "--csv --log-file <CSV> python bench.py --alg merge --steps 1 --warmup 3 --no-extras --forms= "
+                   "--no-clocks")
 
 
 def sources_sha256(paths):
@@ -181,6 +215,45 @@ def gather_aware(kernel, label, m, nnz, k, ns, mean_call, peak, l2_bytes, s_b=4)
         total_ms += mean_call[n]
     return {"formula": "(m+1)*4 + nnz*8 + m*n*4 + nnz*n*4*(1-h) per call", "bytes": total_bytes,
             "frac": total_bytes / (peak * 1e9) * 1e3 / total_ms, "per_n": per_n}
+
+
+def gather_ceiling(b_bytes, row_bytes):
+    """Measured gather ceiling (TB/s of gathered bytes) for uniformly random rows of row_bytes
+    bytes from a B of b_bytes bytes: the committed --sweep gather data, interpolated in log B
+    between the measured sizes (clamped at both ends).  None without the data or the width."""
+    if not os.path.exists(GATHER_JSON):
+        return None
+    pts = sorted((r["b_mb"] * (1 << 20), r["gathered_tb_s"]) for r in map(json.loads, open(GATHER_JSON))
+                 if r["row_bytes"] == row_bytes)
+    if not pts:
+        return None
+    if b_bytes <= pts[0][0]:
+        return pts[0][1]
+    for (b0, t0), (b1, t1) in zip(pts, pts[1:]):
+        if b_bytes <= b1:
+            w = (np.log(b_bytes) - np.log(b0)) / (np.log(b1) - np.log(b0))
+            return float(t0 + w * (t1 - t0))
+    return pts[-1][1]
+
+
+def gather_bound(m, nnz, k, ns, mean_call, slabs_of, s_b=4):
+    """Second roofline: the time the nonzeros' B-row gathers take at the measured gather ceiling
+    (bench.py --sweep gather) for the row width and B (slab) size each call gathers from."""
+    per_n, t_sum, ms_sum = {}, 0.0, 0.0
+    for n in ns:
+        slabs = slabs_of(n)
+        row_bytes = n * s_b // slabs
+        ceil = gather_ceiling(k * row_bytes, row_bytes)
+        if ceil is None:
+            return None
+        t = nnz * n * s_b / (ceil * 1e12) * 1e3
+        per_n[str(n)] = {"row_bytes": row_bytes, "b_slab_bytes": k * row_bytes, "ceiling_tb_s": ceil,
+                         "t_gather_ms": t, "frac": t / mean_call[n]}
+        t_sum += t
+        ms_sum += mean_call[n]
+    return {"source": "profiles/gather_ceiling_sweep.jsonl (bench.py --sweep gather)",
+            "formula": "nnz*n*4 / ceiling(row bytes, B slab bytes) per call", "frac": t_sum / ms_sum,
+            "per_n": per_n}
 
 
 def ingest_ncu(csv_path, out_path=TRAFFIC_JSON):
@@ -452,6 +525,8 @@ def main():
                                    "gflops": 2.0 * nnz * n / (mean_call[n] * 1e-3) / 1e9,
                                    "alg": ALG_NAME[alg_of[n]]} for n in ns},
                 "gather_aware": gather_aware(dom_alg[fam], label, m, nnz, k, fam_ns, mean_call, peak, l2),
+                "gather_bound": gather_bound(m, nnz, k, ns, mean_call,
+                                             lambda n: pkg.default_column_slabs(alg_of[n], k, n, pkg.F32)),
                 "l2_bytes": l2}
 
     line = {"metric": "SpMM GFLOP/s (2*nnz*n/t)", "value": value, "unit": "GFLOP/s", "n_gpus": world,
@@ -462,30 +537,33 @@ def main():
                        "tuning": tuning,
                        "replicas": world, "l2_flush": "2x L2 write before every step", "parallelism": "replicas"},
             "roofline": roofline, "gpu_launches": int(launches),
-            "step_ms_stats": {"median": float(statistics.median(step_ms)), "min": float(min(step_ms)),
-                              "max": float(max(step_ms)), "steps": len(step_ms)}}
+            "ms_per_step_median": float(statistics.median(step_ms)),
+            "step_ms_stats": {"median": float(statistics.median(step_ms)), "mean": float(statistics.mean(step_ms)),
+                              "min": float(min(step_ms)), "max": float(max(step_ms)), "steps": len(step_ms)}}
     cs = clk.summary()
     if cs:
         line["clocks"] = cs
 
     line["selector"] = {"paper_section_5_4": {str(n): ALG_NAME[paper_pick[n]] for n in ns},
                         "gb300": {str(n): ALG_NAME[gb300_pick[n]] for n in ns}}
+    head_rows = sample_rows(m, 4096, 51)
+    head_C = {n: d_C[n][torch.from_numpy(head_rows).to(dev)].cpu().numpy() for n in ns}
     if rank == 0 and not args.no_extras:
         line["breakdown"] = breakdown(pkg, torch, one, ns, nnz, comp, args.steps, flush, stream)
         line["e2e"] = e2e(pkg, torch, a, ns, Bs, args, tuning)
-        if world == 1:
-            g, t, nrows, thr, passes = time_oracle_sample(a, ns, Bs)
-            line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
-                                    "sample": f"{passes} pass(es) over {nrows} seeded random rows of the {label} "
-                                              f"matrix, all n, {t:.1f} s"}
     forms = [f for f in args.forms.split(",") if f]
-    if rank == 0 and forms:
+    if rank == 0 and (forms or not args.no_extras):
         del d_B, d_C, ws
         torch.cuda.empty_cache()
+    if rank == 0 and forms:
         line["forms"] = {}
         for form in forms:
             line["forms"][form] = FORMS[form](pkg, torch, flush, stream, args.steps, args)
             torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
+        line["plain"] = plain_latency(pkg, torch, flush, stream, args.steps)
+        if world == 1:
+            oracle_leg(line, a, ns, Bs, label, head_rows, head_C)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -640,6 +718,13 @@ def form_precision(pkg, torch, flush, stream, steps, args):
     t32 = _time(torch, lambda: pkg.spmm(rp, ci, v32, B32, alg="auto_gb300", out=C32, nnz=nnz, tuning=tun),
                 flush, stream, steps)
     out["f32_plain"] = {"ms": t32, "gflops": flops / t32 / 1e6}
+    # sampled rows for the oracle leg: the original float32 sub-problem, and per variant the same
+    # sub-problem with vals and B rounded as the variant stores them
+    rows = sample_rows(a.m, 4096, 31)
+    rows_d = torch.from_numpy(rows).to(dev)
+    sub = subproblem(rows, a.row_ptr, a.col_ind, a.vals, Bf)
+    SAMPLES["precision/f32_plain"] = dict(sub=sub, sub_rounded=None, C=C32[rows_d].float().cpu().numpy(),
+                                          floor=0.0, tol_rounded=None)
     variants = {"bf16_vals_bf16_B_bf16_C": (torch.bfloat16, torch.bfloat16, torch.bfloat16),
                 "bf16_vals_bf16_B_f32_C": (torch.bfloat16, torch.bfloat16, torch.float32),
                 "bf16_vals_f16_B_f32_C": (torch.bfloat16, torch.float16, torch.float32),
@@ -651,6 +736,13 @@ def form_precision(pkg, torch, flush, stream, steps, args):
                   flush, stream, steps)
         out[name] = {"ms": t, "gflops": flops / t / 1e6, "speedup_vs_f32": t32 / t,
                      "max_norm_diff_vs_f32_path": _norm_diff(torch, C, C32, D)}
+        rnd = lambda x, dt: torch.from_numpy(x).to(dt).double().numpy()
+        sub_r = (sub[0], sub[1], rnd(sub[2], tv), rnd(sub[3], tb))
+        tc_name = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}[tc]
+        SAMPLES["precision/" + name] = dict(
+            sub=sub, sub_rounded=sub_r, C=C[rows_d].float().cpu().numpy(),
+            floor=2.0 ** -25 if tc_name == "f16" else 0.0,
+            tol_rounded={"f32": 1e-5, "bf16": 2.0 ** -8, "f16": 2.0 ** -10}[tc_name])
         del v16, B16, C
     return out
 
@@ -661,7 +753,8 @@ def form_backward(pkg, torch, flush, stream, steps, args):
     dev = torch.device("cuda")
     rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
     v, dX_in = torch.from_numpy(a.vals).to(dev), torch.from_numpy(X).to(dev)
-    dY = torch.randn(a.m, X.shape[1], device=dev, generator=torch.Generator(device=dev).manual_seed(1807))
+    dY_h = gen.normal_matrix(a.m, X.shape[1], gen.SEED_BASE + 4, stream=7)
+    dY = torch.from_numpy(dY_h).to(dev)
     A = pkg.CSRMatrix(rp, ci, (a.m, a.k))
     nnz, n = a.nnz, X.shape[1]
     flops = 2.0 * nnz * n
@@ -688,8 +781,15 @@ def form_backward(pkg, torch, flush, stream, steps, args):
         a.m, a.k, nnz, rp.data_ptr(), ci.data_ptr(), rpt2.data_ptr(), cit2.data_ptr(), perm2.data_ptr(), ws_t.data_ptr(),
         ws_t.numel(), stream.cuda_stream), "spmm_csr_transpose"), flush, stream, steps)
     assert torch.equal(rpt2, rpt) and torch.equal(cit2, cit) and torch.equal(perm2, perm)
-    # the plain float32 kernel on the forward shape, fixed family (reference point of the form)
-    t_plain = _time(torch, lambda: A.spmm(v, dX_in, out=Y, alg=pkg.ALG_ROW_SPLIT), flush, stream, steps)
+    # sampled outputs for the oracle leg: rows of Y, rows of dX (= columns of A), dvals of sampled rows
+    rows = sample_rows(a.m, 2048, 41)
+    cols = sample_rows(a.k, 2048, 42)
+    idx = row_nonzeros(rows, a.row_ptr)
+    SAMPLES["backward"] = dict(a=a, X=X, dY=dY_h, rows=rows, cols=cols, idx=idx,
+                               Y=Y[torch.from_numpy(rows).to(dev)].cpu().numpy(),
+                               dX=dX[torch.from_numpy(cols).to(dev)].cpu().numpy(),
+                               dv=dv[torch.from_numpy(idx).to(dev)].cpu().numpy())
+    step = t_fwd + t_dx + t_sd
     return {"workload": "Chung-Lu GCN 500k, n=256", "nnz": nnz, "mean_degree": a.info["mean_degree"],
             "max_degree": a.info["max_degree"], "transpose_first_call_ms": t_transpose,
             "transpose": {"ms": t_tr, "note": "stable radix sort by column, device time with preallocated "
@@ -698,9 +798,11 @@ def form_backward(pkg, torch, flush, stream, steps, args):
             "forward": {"ms": t_fwd, "gflops": flops / t_fwd / 1e6},
             "dX_AT_dY": {"ms": t_dx, "gflops": flops / t_dx / 1e6, "includes": "vals gather + SpMM on A^T"},
             "dvals_sddmm": {"ms": t_sd, "gflops": flops / t_sd / 1e6},
-            "f32_plain_row_split_forward": {"ms": t_plain, "gflops": flops / t_plain / 1e6},
-            "fwd_bwd_step_ms": t_fwd + t_dx + t_sd,
-            "speedup_fwd_vs_f32_plain": t_plain / t_fwd}
+            "fwd_bwd_step_ms": step,
+            "vs_f32_plain_forward": {
+                "note": "the plain float32 forward SpMM A X on this shape (GB300 selector) is the unit",
+                "dX_over_forward": t_dx / t_fwd, "sddmm_over_forward": t_sd / t_fwd,
+                "step_over_three_forwards": step / (3.0 * t_fwd)}}
 
 
 def form_batched(pkg, torch, flush, stream, steps, args):
@@ -738,6 +840,132 @@ def form_batched(pkg, torch, flush, stream, steps, args):
     return out
 
 
+def plain_latency(pkg, torch, flush, stream, steps):
+    """The plain 4096 x 4096 product (16 nonzeros per row, n = 64, float32): one call with the L2
+    flushed before it, one call warm, and a CUDA graph replaying 100 calls (per call)."""
+    a, B = gen.workload_plain()
+    dev = torch.device("cuda")
+    rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
+    Bd = torch.from_numpy(B).to(dev)
+    n = B.shape[1]
+    C = torch.empty((a.m, n), device=dev)
+    lmax = pkg.max_row_length(rp)
+    tun = {"max_row_len": lmax}
+    alg = pkg.spmm_select_alg_gb300(a.m, a.nnz, lmax, n, pkg.F32)
+    ws_b = max(pkg.workspace_size(a.m, a.k, n, a.nnz, al) for al in (pkg.ALG_MERGE, pkg.ALG_ROW_SPLIT_HYBRID))
+    ws = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=dev)
+
+    def call():
+        pkg.spmm(rp, ci, v, Bd, alg=alg, out=C, nnz=a.nnz, tuning=tun, workspace=ws)
+
+    reps = max(steps, 20)
+    t_flushed = _time(torch, call, flush, stream, reps)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        call()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(100):
+            call()
+    g.replay()
+    torch.cuda.synchronize()
+    def replays(flushed):
+        tg = []
+        for _ in range(5):
+            if flushed:
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tg.append(e0.elapsed_time(e1) / 100.0)
+        return float(statistics.median(tg))
+
+    t_graph = replays(True)
+    t_warm = replays(False)
+    del g
+    SAMPLES["plain"] = dict(a=a, B=B, C=C.cpu().numpy())
+    flops = 2.0 * a.nnz * n
+    comp = compulsory_bytes(a.m, a.nnz, a.k, n)
+    return {"workload": "plain 4096x4096, 16 nonzeros per row, n=64", "nnz": a.nnz, "alg": ALG_NAME[alg],
+            "compulsory_bytes": comp,
+            "l2_flushed_call": {"ms": t_flushed, "gflops": flops / t_flushed / 1e6,
+                                "note": "one call, CUDA events, the L2 flush before it keeps the GPU busy "
+                                        "while the call is enqueued"},
+            "graph_100_calls_after_flush": {"ms_per_call": t_graph, "gflops": flops / t_graph / 1e6,
+                                            "note": "L2 flushed before each replay of 100 back-to-back calls"},
+            "graph_100_calls_warm": {"ms_per_call": t_warm, "gflops": flops / t_warm / 1e6,
+                                     "note": "replays back to back, inputs resident in L2"}}
+
+
+def oracle_leg(line, a, ns, Bs, label, head_rows, head_C):
+    """The cpu_baseline leg: the FP64 oracle timed on a bounded sample of the headline workload, and
+    the sampled GPU results of the headline and the forms checked against it (normalised error
+    max |C - C_ref| / (|A||B|); the 16-bit forms against the oracle on the original float32 inputs
+    and on the inputs rounded as stored)."""
+    import oracle
+
+    g, t, nrows, thr, passes = time_oracle_sample(a, ns, Bs)
+    line["cpu_baseline"] = {"value": g, "unit": "GFLOP/s", "cores": thr, "kind": "oracle",
+                            "sample": f"{passes} pass(es) over {nrows} seeded random rows of the {label} "
+                                      f"matrix, all n, {t:.1f} s"}
+    errs = {}
+    for n in ns:
+        ref = oracle.spmm_rows(head_rows, a.row_ptr, a.col_ind, a.vals, Bs[n])
+        D = oracle.abs_bound_rows(head_rows, a.row_ptr, a.col_ind, a.vals, Bs[n])
+        errs[str(n)] = oracle.normalized_error(head_C[n], ref, D)
+    line["oracle_check"] = {"rows_sampled": int(len(head_rows)), "max_norm_error": errs, "bound": 1e-5}
+    forms = line.get("forms", {})
+    if "precision" in forms:
+        for key, smp in SAMPLES.items():
+            if not key.startswith("precision/"):
+                continue
+            rp, ci, v, Bsub = smp["sub"]
+            e_o = oracle.normalized_error(smp["C"], oracle.spmm(rp, ci, v, Bsub), oracle.abs_bound(rp, ci, v, Bsub),
+                                          abs_floor=smp["floor"])
+            entry = {"vs_original_f32_inputs": e_o, "bound_original": 1e-2 if smp["sub_rounded"] else 1e-5,
+                     "rows_sampled": int(len(rp) - 1)}
+            if smp["sub_rounded"] is not None:
+                rp, ci, v, Bsub = smp["sub_rounded"]
+                entry["vs_rounded_inputs"] = oracle.normalized_error(
+                    smp["C"], oracle.spmm(rp, ci, v, Bsub), oracle.abs_bound(rp, ci, v, Bsub), abs_floor=smp["floor"])
+                entry["bound_rounded"] = smp["tol_rounded"]
+            forms["precision"].setdefault(key.split("/", 1)[1], {})["oracle_error"] = entry
+    if "backward" in forms and "backward" in SAMPLES:
+        smp = SAMPLES["backward"]
+        A, X, dY = smp["a"], smp["X"], smp["dY"]
+        rp, ci, v, Xs = subproblem(smp["rows"], A.row_ptr, A.col_ind, A.vals, X)
+        e_y = oracle.normalized_error(smp["Y"], oracle.spmm(rp, ci, v, Xs), oracle.abs_bound(rp, ci, v, Xs))
+        rpt, cit, perm = oracle.csr_transpose(A.row_ptr, A.col_ind, A.k)
+        rq, cq, vq, dYs = subproblem(smp["cols"], rpt, cit, A.vals[perm], dY)
+        e_dx = oracle.normalized_error(smp["dX"], oracle.spmm(rq, cq, vq, dYs), oracle.abs_bound(rq, cq, vq, dYs))
+        dYr = dY[smp["rows"]]
+        e_dv = oracle.normalized_error(smp["dv"], oracle.sddmm(rp, ci, dYr, Xs), oracle.sddmm_abs_bound(rp, ci, dYr, Xs))
+        forms["backward"]["oracle_error"] = {"forward_rows": e_y, "dX_rows": e_dx, "dvals_of_rows": e_dv,
+                                             "rows_sampled": int(len(smp["rows"])), "bound": 1e-5}
+    if "plain" in line and "plain" in SAMPLES:
+        smp = SAMPLES["plain"]
+        pa, B = smp["a"], smp["B"]
+        ref = oracle.spmm(pa.row_ptr, pa.col_ind, pa.vals, B)
+        line["plain"]["oracle_error"] = oracle.normalized_error(
+            smp["C"], ref, oracle.abs_bound(pa.row_ptr, pa.col_ind, pa.vals, B))
+        threads = oracle.num_threads()
+        oracle.set_threads(1)
+        try:
+            reps, t0 = 0, time.perf_counter()
+            while reps < 3 or time.perf_counter() - t0 < 1.0:
+                oracle.spmm(pa.row_ptr, pa.col_ind, pa.vals, B)
+                reps += 1
+            t1 = (time.perf_counter() - t0) / reps
+        finally:
+            oracle.set_threads(threads)
+        line["plain"]["oracle_one_thread"] = {"ms": t1 * 1e3, "gflops": 2.0 * pa.nnz * B.shape[1] / t1 / 1e9}
+
+
 FORMS = {"precision": form_precision, "backward": form_backward, "batched": form_batched}
 
 
@@ -757,6 +985,8 @@ def run_sweep(args):
     reps = max(3, min(args.steps, 5))
     n = 64
     name = ALG_NAME
+    if args.sweep == "gather":
+        return run_gather_sweep(pkg, torch, dev, flush, stream, reps)
     if args.sweep == "aspect":
         # dense matrices stored as CSR, from 2 rows of 2^23 nonzeros to 2^23 rows of 2 (the paper's Fig. 1 / Fig. 4)
         total = 1 << 24
@@ -812,7 +1042,8 @@ def run_sweep(args):
         # fixed fraction of nonzeros per row of a 100k x 100k matrix vs dense GEMM (the paper's Fig. 7)
         mk = 100_000
         B = torch.randn(mk, n, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
-        for frac in (0.0001, 0.001, 0.005, 0.01, 0.02, 0.05, 0.1):
+        # up to 21 %: nnz = 2.1e9 keeps every index below 2^31
+        for frac in (0.0001, 0.001, 0.005, 0.01, 0.02, 0.05, 0.1, 0.12, 0.15, 0.18, 0.21):
             per_row = max(1, int(round(frac * mk)))
             a = gen.uniform_rows(mk, mk, per_row, gen.SEED_BASE + 70)
             rp, ci, v = (torch.from_numpy(x).to(dev) for x in (a.row_ptr, a.col_ind, a.vals))
@@ -842,6 +1073,31 @@ def run_sweep(args):
             print(json.dumps(row), flush=True)
             del rp, ci, v, C, dense
             torch.cuda.empty_cache()
+    return 0
+
+
+def run_gather_sweep(pkg, torch, dev, flush, stream, reps):
+    """The gather-only probe (spmm_gather_probe): 2^24 rows of B read at uniformly random row
+    indices, lane groups of row_bytes / 16 lanes, eight rows in flight per lane, over every SM;
+    B from 16 MB to 1 GB, rows of 32-512 bytes.  Gathered TB/s and gathers per second per point
+    (L2 flushed before each run, median of the runs)."""
+    count = 1 << 24
+    g = torch.Generator(device=dev).manual_seed(93)
+    out = torch.zeros(1, dtype=torch.int32, device=dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    for mb in (16, 32, 48, 64, 80, 96, 128, 192, 256, 512, 1024):
+        buf = torch.empty(mb << 20, dtype=torch.uint8, device=dev)
+        buf.fill_(1)
+        for rb in (32, 64, 128, 256, 512):
+            rows = (mb << 20) // rb
+            idx = torch.randint(rows, (count,), generator=g, device=dev, dtype=torch.int32)
+            t = _time(torch, lambda: pkg.gather_probe(buf, idx, rb, out), flush, stream, reps)
+            print(json.dumps({"sweep": "gather", "b_mb": mb, "row_bytes": rb, "gathers": count, "ms": t,
+                              "gathered_tb_s": count * rb / t / 1e9, "g_gathers_per_s": count / t / 1e6,
+                              "l2_bytes": l2}), flush=True)
+            del idx
+        del buf
+        torch.cuda.empty_cache()
     return 0
 
 

@@ -158,6 +158,16 @@ int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, in
 double spmm_tiled_reuse(int m, int k, long long nnz, int n, int b_type);
 
 /*
+ * Column slabs the library uses by default for a product of algorithm alg
+ * (a spmm_alg_t after selection) with k rows of B and n columns of b_type on
+ * the current device: 2 when B is larger than twice the device's L2 and its
+ * rows are wide (>= 512 bytes for merge, >= 256 bytes otherwise), else 1.
+ * Each slab pass gathers that share of every row of B from a B slab that
+ * much smaller.  Reads the L2 size of the current device (no device work).
+ */
+int spmm_default_column_slabs(int alg, int k, int n, int b_type);
+
+/*
  * Longest row of A (max over i of row_ptr[i+1] - row_ptr[i]) computed on the
  * device and written to *max_row_len (host).  Synchronises `stream`.  Uses a
  * 4-byte stream-ordered device allocation.
@@ -249,10 +259,13 @@ int spmm_merge_partition(int m, long long nnz, const int *row_ptr, int items_per
  * (SPMM_ALG_AUTO_GB300 without tuning->max_row_len scans the host row_ptr for
  * the longest row).  Copies and compute are pipelined: B and C in column
  * slabs, A in up to four row chunks, so that the first block is computed as
- * soon as its pieces are on the device.  Device buffers come stream-ordered
- * from a memory pool of the library's own (one per device; freed memory stays
- * cached in it until exit) and are released before return.  Pinned
- * (page-locked) host buffers make the copies asynchronous DMA.
+ * soon as its pieces are on the device.  The uploads run on a copy stream of
+ * the library's own, after all work queued on `stream` before the call, so a
+ * host input that such work writes (a D2H copy, an earlier
+ * spmm_csr_host_async) is read once it is written.  Device buffers come
+ * stream-ordered from a memory pool of the library's own (one per device;
+ * freed memory stays cached in it until exit) and are released before return.
+ * Pinned (page-locked) host buffers make the copies asynchronous DMA.
  */
 int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
                   int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,
@@ -264,11 +277,17 @@ int spmm_csr_host(int m, int k, int n, const int *row_ptr, const int *col_ind, c
  * result once `stream` has been synchronised, or once an event recorded on
  * `stream` after the call has completed, and work queued on `stream` after the
  * call runs after C has arrived.  row_ptr is read on the host during the call; every
- * host buffer must stay valid, and A and B unmodified, until then.  With
- * pinned host buffers, back-to-back calls overlap: a call's uploads run while
- * the previous call's last blocks of C are still coming down.  Arguments,
- * pipelining and errors as in spmm_csr_host; an error of a queued copy or
- * kernel is reported by the synchronisation, not by this call.
+ * host buffer must stay valid, and A and B unmodified, until then.  Unlike
+ * spmm_csr_host, the uploads are NOT ordered after work queued on `stream`
+ * before the call: they start on the library's copy stream at once, so host
+ * inputs must hold their final values when the call is made (the C of an
+ * earlier asynchronous call becomes a valid input only after a
+ * synchronisation of `stream`, or of an event recorded on it after that
+ * call).  In exchange, with pinned host buffers, back-to-back calls overlap: a
+ * call's uploads run while the previous call's last blocks of C are still
+ * coming down.  Arguments, pipelining and errors as in spmm_csr_host; an error
+ * of a queued copy or kernel is reported by the synchronisation, not by this
+ * call.
  */
 int spmm_csr_host_async(int m, int k, int n, const int *row_ptr, const int *col_ind, const void *vals,
                         int vals_type, const void *B, int b_type, long long ldb, void *C, int c_type,
@@ -282,6 +301,22 @@ int spmm_csr_host_async(int m, int k, int n, const int *row_ptr, const int *col_
  * context stays usable.  Not part of the paper; used by the failure tests.
  */
 int spmm_debug_bounded_wait(int *d_status, long long limit_ns, void *stream);
+
+/*
+ * Gather-rate probe (measurement only; the paper has no counterpart, though
+ * the access it times is the one Section 4.1 singles out: one row of B read
+ * per nonzero with coalesced accesses).  Reads count rows of row_bytes bytes
+ * (16, 32, 64, 128, 256 or 512) of the device array B (rows rows, row r at
+ * byte offset r * row_bytes, B 16-byte aligned) at the row indices idx[0 ..
+ * count) (device int array; an index outside [0, rows) is skipped), with
+ * lane groups of row_bytes / 16 lanes and eight rows in flight per lane as in
+ * the SpMM kernels, and XORs every 32-bit word read into *out (a device
+ * word the caller initialises).  Timing it over B sizes and row widths gives
+ * the gather ceilings and the effective L2 capacity that bound the SpMM
+ * rooflines.  Asynchronous on `stream`.
+ */
+int spmm_gather_probe(const void *B, long long rows, int row_bytes, const int *idx, long long count,
+                      unsigned *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Backward of C = A B (not in the paper, which names SpMM_T only as future
@@ -401,14 +436,17 @@ int spmm_autotune_cache_clear(void);
  *
  * The merge-based path keeps its scratch in one fixed array of
  * spmm_csr_static_scratch_bytes() bytes (16 MiB) in device global memory,
- * reserved on every device that loads the library and held until the process
- * exits.  Problems whose merge scratch (spmm_csr_workspace_size) exceeds it
- * are rejected with SPMM_ERR_WORKSPACE before any device work.  Row split
- * needs no scratch.  The call makes no cudaMalloc / cudaFree or other
- * allocating call.
+ * held until the process exits.  Problems whose merge scratch for the launch
+ * shape the call picks exceeds it (at most spmm_csr_workspace_size(...), which
+ * sizes for every shape) are rejected with SPMM_ERR_WORKSPACE before any
+ * device work.  Row split needs no scratch.  The call itself makes no
+ * cudaMalloc / cudaFree or other allocating call.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first merge-path call on a device looks up the array's device address
+ * (cudaGetSymbolAddress).  CUDA loads a library's device code lazily by
+ * default, so that first call may also be the moment the library's code is
+ * loaded on the device and the array reserved, and it can then fail for lack
+ * of device memory: make it during set-up, and before any stream capture.
  * Every call shares the one array and leaves its contents behind; nothing in
  * it needs to start at zero, but calls that overlap on the GPU (on different
  * streams, or from several threads) race on it: serialise them.

@@ -61,6 +61,8 @@ _SIGNATURES = {
     "spmm_launch_count": ([], _ll),
     "spmm_select_alg": ([_i, _ll, _d], _i),
     "spmm_select_alg_gb300": ([_i, _ll, _ll, _i, _i], _i),
+    "spmm_gather_probe": ([_vp, _ll, _i, _vp, _ll, _vp, _vp], _i),
+    "spmm_default_column_slabs": ([_i, _i, _i, _i], _i),
     "spmm_tiled_reuse": ([_i, _i, _ll, _i, _i], _d),
     "spmm_csr_max_row_length": ([_i, _vp, ctypes.POINTER(_ll), _vp], _i),
     "spmm_csr": ([_i, _i, _i, _vp, _vp, _vp, _vp, _ll, _vp, _ll, _i, _vp], _i),
@@ -141,6 +143,19 @@ def spmm_csr_max_row_length(m, row_ptr, stream) -> tuple[int, int]:
     out = ctypes.c_longlong(0)
     st = load().spmm_csr_max_row_length(m, row_ptr, ctypes.byref(out), stream)
     return st, out.value
+
+
+def default_column_slabs(alg: int, k: int, n: int, b_type: int = F32) -> int:
+    return load().spmm_default_column_slabs(alg, k, n, b_type)
+
+
+def gather_probe(B, idx, row_bytes: int, out, stream=None) -> None:
+    """spmm_gather_probe on a CUDA tensor B (bytes viewed as rows of row_bytes), int32 CUDA
+    indices idx and a one-word int32 CUDA tensor out (XOR of the words read)."""
+    _require_cuda(B, idx, out)
+    nbytes = B.numel() * B.element_size()
+    _check(load().spmm_gather_probe(B.data_ptr(), nbytes // row_bytes, row_bytes, idx.data_ptr(), idx.numel(),
+                                    out.data_ptr(), _stream_handle(stream)), "spmm_gather_probe")
 
 
 def max_row_length(row_ptr, stream=None) -> int:
@@ -346,7 +361,10 @@ def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None
     ``wait=True`` (``spmm_csr_host``) the call returns once C is filled; with
     ``wait=False`` (``spmm_csr_host_async``) it returns once the work is queued,
     and C is filled when ``stream`` (default: torch's current stream) has been
-    synchronised; the operands must stay alive and A, B unchanged until then."""
+    synchronised; the operands must stay alive and A, B unchanged until then.
+    The synchronous call reads its inputs after the work already queued on
+    ``stream``; the asynchronous one reads them from call time on (the C of an
+    earlier asynchronous call is a valid input only after a synchronisation)."""
     for t in (row_ptr, col_ind, vals, B, C):
         if t.is_cuda:
             raise ValueError("spmm_host takes host tensors")

@@ -609,6 +609,11 @@ double spmm_tiled_reuse(int m, int k, long long nnz, int n, int b_type) {
     return rows_per_block * (double)nnz / ((double)m * (double)k);
 }
 
+int spmm_default_column_slabs(int alg, int k, int n, int b_type) {
+    if (k < 0 || n < 0 || dtype_size(b_type) == 0) return 1;
+    return spmm::default_slabs(alg, k, n, b_type);
+}
+
 int spmm_csr_max_row_length(int m, const int* row_ptr, long long* max_row_len, void* stream) {
     if (m < 0 || !max_row_len || (m > 0 && !row_ptr)) return SPMM_ERR_INVALID_VALUE;
     *max_row_len = 0;
@@ -779,7 +784,7 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
     total = off_ws + align256(ws_need);
     cudaMemPool_t pool = host_staging_pool();
     if (!pool) return SPMM_ERR_CUDA;
-    std::vector<cudaEvent_t> ev(3 + chunks + slabs + (size_t)slabs * chunks, nullptr);
+    std::vector<cudaEvent_t> ev(4 + chunks + slabs + (size_t)slabs * chunks, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
@@ -790,6 +795,18 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
     if (e != cudaSuccess) {
         destroy_events();
         return cuda_status(e);
+    }
+    // The synchronous entry orders its uploads after the work already queued on `stream` (which may
+    // write the host inputs); the asynchronous entry reads them from call time on, so that its uploads
+    // can overlap the previous call's downloads.
+    if (wait) {
+        cudaEvent_t e_in = ev[3 + chunks + slabs + (size_t)slabs * chunks];
+        e = cudaEventRecord(e_in, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_in, 0);
+        if (e != cudaSuccess) {
+            destroy_events();
+            return cuda_status(e);
+        }
     }
     // The buffer is allocated in the upload stream's order, so the uploads need no other wait;
     // compute and downloads reach it only through events recorded after those uploads.

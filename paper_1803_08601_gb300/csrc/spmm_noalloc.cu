@@ -10,8 +10,9 @@
 //
 // The merge-based path needs scratch memory (tile boundaries, and the partial
 // sums of rows that cross tiles).  Here that scratch is a fixed array in
-// device global memory, reserved when the library is loaded on a device and
-// held until the process exits.
+// device global memory, reserved when the library's device code is loaded on
+// a device (with CUDA's default lazy loading, at the first merge-path call on
+// that device) and held until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -72,9 +73,8 @@ int spmm_csr_noalloc(int m, int k, int n, long long nnz, const int* row_ptr, con
     if (a != SPMM_ALG_MERGE)  // row split needs no scratch
         return spmm_csr_ex(m, k, n, nnz, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, a,
                            tuning, nullptr, 0, d_status, stream);
-    const size_t need = spmm_csr_workspace_size(m, k, n, nnz, SPMM_ALG_MERGE, b_type, tuning);
-    if (need == 0) return SPMM_ERR_INVALID_VALUE;
-    if (need > kStaticScratchBytes) return SPMM_ERR_WORKSPACE;  // problem too large for the fixed scratch
+    // spmm_csr_ex checks the exact scratch of the launch shape it picks against the array's size and
+    // returns SPMM_ERR_WORKSPACE, before any device work, when the problem does not fit
     void* ws = nullptr;
     const int st = scratch_address(&ws);
     if (st != SPMM_OK) return st;

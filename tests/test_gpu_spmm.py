@@ -405,6 +405,41 @@ def test_host_async_back_to_back(gpu_lib):
         assert torch.equal(c0, c1)
 
 
+def test_host_calls_chained_through_host_memory(gpu_lib):
+    """The C of an asynchronous host-buffer call is the B of the next call.  The
+    synchronous entry orders its uploads after the work already queued on the
+    stream, so it reads the finished C with no synchronisation in between (C
+    starts as NaN: a stale read would show).  The asynchronous entry reads its
+    inputs from call time on, so it is handed C after a synchronisation; both
+    chains give the same bits."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(31)
+    m1, k1, m2, n = 60_000, 40_000, 30_000, 64
+    a1 = csr_arrays(rng.integers(0, 40, m1), k1, 32)
+    a2 = csr_arrays(rng.integers(0, 40, m2), m1, 33)
+    A1 = tuple(torch.from_numpy(x).pin_memory() for x in a1)
+    A2 = tuple(torch.from_numpy(x).pin_memory() for x in a2)
+    B1 = torch.from_numpy(gen.normal_matrix(k1, n, 34)).pin_memory()
+    stream = torch.cuda.current_stream()
+    outs = []
+    for chain in ("sync_after_async", "async_after_sync"):
+        C1 = torch.full((m1, n), float("nan")).pin_memory()
+        C2 = torch.full((m2, n), float("nan")).pin_memory()
+        pkg.spmm_host(*A1, B1, C1, alg="auto_gb300", wait=False)
+        if chain == "sync_after_async":
+            pkg.spmm_host(*A2, C1, C2, alg="auto_gb300", wait=True)
+        else:
+            stream.synchronize()
+            pkg.spmm_host(*A2, C1, C2, alg="auto_gb300", wait=False)
+            stream.synchronize()
+        check(C1.numpy(), *a1, B1.numpy())
+        check(C2.numpy(), *a2, C1.numpy())
+        outs.append((C1, C2))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
 def test_host_entry_few_long_rows(gpu_lib):
     """Three rows of two million nonzeros: at most as many chunks as rows."""
     import torch

@@ -42,8 +42,10 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls(gpu_lib, alg):
         C_new = _noalloc(pkg, torch, d_rp, d_ci, d_v, d_B, nnz, alg)
         C_ref = pkg.spmm(d_rp, d_ci, d_v, d_B, alg=alg, nnz=int(rp[-1]))
         torch.cuda.synchronize()
+        # the same kernels and tiles: the same bits, whatever the previous call left in the scratch
+        assert torch.equal(C_new, C_ref)
         D = oracle.abs_bound(rp, ci, v, B)
-        assert oracle.normalized_error(C_new.cpu().numpy(), C_ref.cpu().numpy(), D) <= FP32_TOL
+        assert oracle.normalized_error(C_new.cpu().numpy(), oracle.spmm(rp, ci, v, B), D) <= FP32_TOL
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(gpu_lib):
@@ -76,9 +78,10 @@ def test_noalloc_spmv_matches_bitwise(gpu_lib, alg):
 
 def test_noalloc_accepts_only_its_documented_algorithms():
     """AUTO, ROW_SPLIT and MERGE only: AUTO_GB300 would allocate to measure the longest row, and
-    the A/B tiling is not offered here; both are rejected before any device work."""
+    neither the A/B tiling nor the hybrid row split (whose queue needs scratch) is offered here;
+    they are rejected before any device work."""
     import paper_1803_08601_gb300 as pkg
 
-    for alg in (pkg.ALG_AUTO_GB300, pkg.ALG_TILED):
+    for alg in (pkg.ALG_AUTO_GB300, pkg.ALG_TILED, pkg.ALG_ROW_SPLIT_HYBRID):
         st = pkg.spmm_csr_noalloc(4, 4, 4, 4, 8, 16, 32, pkg.F32, 64, pkg.F32, 4, 128, pkg.F32, 4, alg, None, None, None)
         assert st == pkg.ERR_INVALID_VALUE
