@@ -381,7 +381,10 @@ typedef struct {
 typedef struct spmm_batched_plan spmm_batched_plan_t; /* opaque */
 
 typedef enum {
-    SPMM_BATCHED_MODEL = 0,     /* per matrix: spmm_select_alg_gb300 (longest rows read at plan time) */
+    SPMM_BATCHED_MODEL = 0,     /* per matrix: merge based when the longest row trips the Type 1
+                                   guard of spmm_select_alg_gb300 (longest rows read at plan
+                                   time), row split otherwise: inside the batch the merge tiles
+                                   run about 2x slower than the row chunks                      */
     SPMM_BATCHED_AUTOTUNE = 1,  /* per matrix: the autotuner's pick for its shape bucket            */
     SPMM_BATCHED_ROW_SPLIT = 2, /* every matrix row split                                            */
     SPMM_BATCHED_MERGE = 3      /* every matrix merge based                                          */
@@ -394,14 +397,21 @@ typedef enum {
  * one device allocation (work list, merge partitions, carry buffers) and
  * synchronises `stream` once.  SPMM_BATCHED_AUTOTUNE times, for every shape
  * bucket (n, floor(log2 m), mean row length class) not yet in the process-wide
- * cache, row split and merge based with three tile sizes on up to 8 of the
- * plan's matrices of that bucket, and keeps the fastest.
+ * cache, row split with the full lane group of the width and with a half and a
+ * quarter of it (twice and four times the column slabs), and merge based with
+ * three tile sizes, on a sample of the plan's matrices of that bucket (up to
+ * 64 matrices or 4M rows + nonzeros), and keeps the fastest.
  */
 int spmm_batched_plan_create(int count, const spmm_batch_matrix_t *mats, int policy, void *stream,
                              spmm_batched_plan_t **plan);
 
-/* Enqueue the batch: a persistent kernel over the merge tiles, a persistent
-   kernel over the row-split chunks and the fix-up (up to three launches). */
+/* Enqueue the batch: a persistent kernel over the row-split chunks (on a
+   stream of the plan's own, forked from and joined back to `stream`, when the
+   plan also has merge tiles), a persistent kernel over the merge tiles and the
+   fix-up (up to three launches, after a memset of the work counters).  Both
+   persistent kernels take their work items from a counter, in the plan's
+   order: row chunks of the largest matrices first.  Runs of one plan share its
+   counters and carry buffers: they must not overlap on the GPU. */
 int spmm_batched_run(const spmm_batched_plan_t *plan, void *stream);
 
 /* Capture spmm_batched_run into a CUDA graph owned by the plan (replaces a

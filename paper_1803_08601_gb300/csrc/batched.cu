@@ -88,11 +88,25 @@ __device__ __forceinline__ void batched_tile(const MatDesc& d, int* carry_row_al
     __syncthreads();
 }
 
+// Next work item of a persistent CTA: taken from a counter (zeroed before the
+// launch), so that the items in flight at any moment are a contiguous window
+// of the plan's item list (largest matrices first) rather than spreading as
+// fast and slow CTAs drift apart: fewer matrices' B rows then share the L2.
+__device__ __forceinline__ long long next_item(unsigned long long* counter) {
+    __shared__ long long s_item;
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long it = s_item;
+    __syncthreads();
+    return it;
+}
+
 // Row-split items: a lean kernel of its own (no shared memory, the row
 // split's registers), so that it runs at the occupancy of the row split.
 __global__ void __launch_bounds__(kThreads)
-    batched_rows_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items) {
-    for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    batched_rows_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
+                        unsigned long long* counter) {
+    for (long long it = next_item(counter); it < n_items; it = next_item(counter)) {
         const Item item = items[it];
         const MatDesc d = mats[item.mat];
         const int slab = item.kind_slab >> 1;
@@ -111,9 +125,9 @@ __global__ void __launch_bounds__(kThreads)
 // worst-case tile variant at 80.
 __global__ void __launch_bounds__(kThreads, 3)
     batched_tiles_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
-                         int* carry_row_all, int* head_row_all, int* status) {
+                         int* carry_row_all, int* head_row_all, int* status, unsigned long long* counter) {
     extern __shared__ __align__(128) unsigned char smem[];
-    for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    for (long long it = next_item(counter); it < n_items; it = next_item(counter)) {
         const Item item = items[it];
         const MatDesc d = mats[item.mat];
         const int slab = item.kind_slab >> 1;
@@ -201,7 +215,10 @@ size_t merge_smem_bytes(int W, int ips) {
 struct Choice {
     int alg;
     int ips_scale;  // merge: ips = default * 2^ips_scale (ips_scale in {-1, 0, 1})
+    int lanes_div;  // row split: lanes per row = lanes_for(n) / lanes_div (1, 2 or 4; more column slabs)
 };
+
+int lanes_of(int n, int lanes_div) { return std::max(1, lanes_for(std::max(n, 1)) / std::max(1, lanes_div)); }
 
 using BucketKey = std::tuple<int, int, int, int>;  // (device SMs, n, floor(log2 m), mean-row-length bucket)
 std::mutex g_tune_mu;
@@ -224,6 +241,7 @@ struct spmm_batched_plan {
     int count = 0;
     std::vector<int> algs;
     std::vector<int> ips;
+    std::vector<int> lanes;  // lanes per row of each matrix
     unsigned char* mem = nullptr;
     MatDesc* d_mats = nullptr;
     Item* d_items = nullptr;       // row-split items, then merge-tile items
@@ -235,6 +253,9 @@ struct spmm_batched_plan {
     int* d_carry_row = nullptr;
     int* d_head_row = nullptr;
     int* d_status = nullptr;
+    unsigned long long* d_counters = nullptr;  // work-item counters of the two persistent kernels
+    cudaStream_t side = nullptr;                // the row-split kernel runs here, beside the merge tiles
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t smem = 0;
     int grid = 0;
     cudaGraphExec_t exec = nullptr;
@@ -248,17 +269,21 @@ namespace {
 void destroy_plan(spmm_batched_plan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->side) cudaStreamDestroy(p->side);
     if (p->mem) cudaFree(p->mem);
     delete p;
 }
 
 // Build a plan for matrices `mats` with per-matrix (alg, ips) already chosen.
 int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<int>& algs, const std::vector<int>& ips,
-               cudaStream_t s, spmm_batched_plan** out) {
+               const std::vector<int>& lanes, cudaStream_t s, spmm_batched_plan** out) {
     auto* p = new spmm_batched_plan();
     p->count = (int)mats.size();
     p->algs = algs;
     p->ips = ips;
+    p->lanes = lanes;
     p->mats = mats;
     cudaGetDevice(&p->device);
     std::vector<MatDesc> descs(mats.size());
@@ -282,7 +307,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
         d.B = mt.B;
         d.C = mt.C;
         d.alg = algs[b];
-        d.W = lanes_for(mt.n);
+        d.W = lanes[b];
         d.slabs = ((mt.n + 3) / 4 + d.W - 1) / d.W;
         d.ips = ips[b];
         d.tile_base = (int)tile_mat.size();
@@ -345,6 +370,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     float* head = reinterpret_cast<float*>(q);
     q += sz_carry;
     p->d_status = reinterpret_cast<int*>(q);
+    p->d_counters = reinterpret_cast<unsigned long long*>(q + 16);
     size_t lim_off = 0, carry_off = 0;
     int st = SPMM_OK;
     for (size_t b = 0; b < descs.size() && st == SPMM_OK; ++b) {
@@ -376,6 +402,11 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     if (st == SPMM_OK)
         st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_rows, batched_rows_kernel, kThreads, 0));
     if (st == SPMM_OK) st = status_of(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (st == SPMM_OK && p->n_row_items > 0 && p->n_items > p->n_row_items) {
+        st = status_of(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+        if (st == SPMM_OK) st = status_of(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+        if (st == SPMM_OK) st = status_of(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
     if (st != SPMM_OK) {
         destroy_plan(p);
         return st;
@@ -388,40 +419,61 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     return SPMM_OK;
 }
 
+// One run: zero the work counters, then the row-split kernel (on the plan's side stream when the
+// plan also has merge tiles, so that the two persistent kernels share the GPU) and the merge-tile
+// kernel followed by the fix-up on `s`; `s` then waits for the side stream.
 int run_plan(const spmm_batched_plan* p, cudaStream_t s) {
     const long long n_tile_items = p->n_items - p->n_row_items;
-    if (n_tile_items > 0) {
-        batched_tiles_kernel<<<p->grid, kThreads, p->smem, s>>>(p->d_mats, p->d_items + p->n_row_items, n_tile_items,
-                                                               p->d_carry_row, p->d_head_row, p->d_status);
-        const cudaError_t e = cudaGetLastError();
+    if (p->n_items > 0) {
+        const cudaError_t e = cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return status_of(e);
-        g_launches.fetch_add(1, std::memory_order_relaxed);
     }
+    const bool fork = p->side && n_tile_items > 0 && p->n_row_items > 0;
+    cudaStream_t rs = s;
+    if (fork) {
+        cudaError_t e = cudaEventRecord(p->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+        if (e != cudaSuccess) return status_of(e);
+        rs = p->side;
+    }
+    int st = SPMM_OK;
     if (p->n_row_items > 0) {
-        batched_rows_kernel<<<p->grid_rows, kThreads, 0, s>>>(p->d_mats, p->d_items, p->n_row_items);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return status_of(e);
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        batched_rows_kernel<<<p->grid_rows, kThreads, 0, rs>>>(p->d_mats, p->d_items, p->n_row_items,
+                                                               p->d_counters + 1);
+        st = status_of(cudaGetLastError());
+        if (st == SPMM_OK) g_launches.fetch_add(1, std::memory_order_relaxed);
     }
-    if (p->total_tiles > 1) {
+    if (st == SPMM_OK && n_tile_items > 0) {
+        batched_tiles_kernel<<<p->grid, kThreads, p->smem, s>>>(p->d_mats, p->d_items + p->n_row_items, n_tile_items,
+                                                               p->d_carry_row, p->d_head_row, p->d_status,
+                                                               p->d_counters);
+        st = status_of(cudaGetLastError());
+        if (st == SPMM_OK) g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (st == SPMM_OK && p->total_tiles > 1) {
         batched_fixup_kernel<<<p->total_tiles, 128, 0, s>>>(p->d_mats, p->d_tile_mat, p->total_tiles, p->d_carry_row,
                                                            p->d_head_row, p->d_status);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return status_of(e);
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        st = status_of(cudaGetLastError());
+        if (st == SPMM_OK) g_launches.fetch_add(1, std::memory_order_relaxed);
     }
-    return SPMM_OK;
+    if (fork) {  // joined whatever happened above, so that a capture ends with every stream joined
+        cudaError_t e = cudaEventRecord(p->ev_join, p->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+        if (st == SPMM_OK && e != cudaSuccess) st = status_of(e);
+    }
+    return st;
 }
 
 // Time one candidate schedule for a sample of matrices (median of 3 runs, ms).
-float time_candidate(const std::vector<spmm_batch_matrix_t>& sample, int alg, int ips_scale, cudaStream_t s) {
-    std::vector<int> algs(sample.size(), alg), ips(sample.size());
+float time_candidate(const std::vector<spmm_batch_matrix_t>& sample, const Choice& c, cudaStream_t s) {
+    std::vector<int> algs(sample.size(), c.alg), ips(sample.size()), lanes(sample.size());
     for (size_t i = 0; i < sample.size(); ++i) {
-        const int d = default_ips(lanes_for(sample[i].n));
-        ips[i] = ips_scale > 0 ? d * 2 : ips_scale < 0 ? std::max(4, d / 2) : d;
+        lanes[i] = c.alg == SPMM_ALG_MERGE ? lanes_for(std::max(sample[i].n, 1)) : lanes_of(sample[i].n, c.lanes_div);
+        const int d = default_ips(lanes[i]);
+        ips[i] = c.ips_scale > 0 ? d * 2 : c.ips_scale < 0 ? std::max(4, d / 2) : d;
     }
     spmm_batched_plan* p = nullptr;
-    if (build_plan(sample, algs, ips, s, &p) != SPMM_OK) return INFINITY;
+    if (build_plan(sample, algs, ips, lanes, s, &p) != SPMM_OK) return INFINITY;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -502,40 +554,65 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
                 sample.push_back(v[kv.second[i]]);
                 work += v[kv.second[i]].m + v[kv.second[i]].nnz;
             }
-            Choice best{SPMM_ALG_ROW_SPLIT, 0};
-            float best_ms = time_candidate(sample, SPMM_ALG_ROW_SPLIT, 0, s);
-            for (int sc : {0, -1, 1}) {
-                const float ms = time_candidate(sample, SPMM_ALG_MERGE, sc, s);
+            // In the full batch a bucket's matrices run on a GPU kept busy by the rest of the batch; a
+            // small sample alone would be timed on its tail.  Repeat the sample (same matrices, same
+            // outputs, identical values written) until it holds 32M rows + nonzeros, at most 32 times.
+            const size_t base = sample.size();
+            for (int rep = 1; rep < 32 && work > 0 && work < (32LL << 20); ++rep) {
+                long long w = 0;
+                for (size_t i = 0; i < base; ++i) {
+                    sample.push_back(sample[i]);
+                    w += sample[i].m + sample[i].nnz;
+                }
+                work += w;
+            }
+            // candidates: row split with the full lane group and with 1/2 and 1/4 of it (column
+            // slabs), merge based with three tile sizes
+            std::vector<Choice> cands = {{SPMM_ALG_ROW_SPLIT, 0, 1}, {SPMM_ALG_ROW_SPLIT, 0, 2},
+                                         {SPMM_ALG_ROW_SPLIT, 0, 4}, {SPMM_ALG_MERGE, 0, 1},
+                                         {SPMM_ALG_MERGE, -1, 1}, {SPMM_ALG_MERGE, 1, 1}};
+            Choice best = cands[0];
+            float best_ms = INFINITY;
+            const int n0 = v[kv.second[0]].n;  // every matrix of a bucket has the same n
+            for (const Choice& c : cands) {
+                if (c.lanes_div > 1 && lanes_of(n0, c.lanes_div) == lanes_of(n0, c.lanes_div / 2))
+                    continue;  // no narrower lane group for this width
+                const float ms = time_candidate(sample, c, s);
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = Choice{SPMM_ALG_MERGE, sc};
+                    best = c;
                 }
             }
             std::lock_guard<std::mutex> lock(g_tune_mu);
             g_tune_cache[kv.first] = best;
         }
     }
+    std::vector<int> lanes(v.size());
     for (size_t b = 0; b < v.size(); ++b) {
-        const int W = lanes_for(std::max(v[b].n, 1));
-        int alg = SPMM_ALG_ROW_SPLIT, sc = 0;
-        if (policy == SPMM_BATCHED_MERGE) alg = SPMM_ALG_MERGE;
-        else if (policy == SPMM_BATCHED_MODEL) {
-            alg = spmm_select_alg_gb300(v[b].m, v[b].nnz, lmax[b], v[b].n, SPMM_F32);
-            // the batched kernels balance a matrix's long rows by merge tiles (no segment queue)
-            if (alg == SPMM_ALG_ROW_SPLIT_HYBRID) alg = SPMM_ALG_MERGE;
-        }
-        else if (policy == SPMM_BATCHED_AUTOTUNE) {
+        int alg = SPMM_ALG_ROW_SPLIT, sc = 0, div = 1;
+        if (policy == SPMM_BATCHED_MERGE) {
+            alg = SPMM_ALG_MERGE;
+        } else if (policy == SPMM_BATCHED_MODEL) {
+            // Inside the batch the merge tiles run about 2x slower than the row chunks (no bulk-copy
+            // staging, 24 warps per SM; measured on the 2048-matrix batch: every matrix merge 23.9 ms,
+            // every matrix row split 10.7 ms), so merge only where the longest row would make the
+            // matrix's row chunks the critical path (the Type 1 guard of the GB300 selector)
+            const bool type1 = lmax[b] > 1024 && lmax[b] * 8192 > v[b].nnz;
+            alg = type1 ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT;
+        } else if (policy == SPMM_BATCHED_AUTOTUNE) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             const Choice c = g_tune_cache[bucket_of(sms, v[b])];
             alg = c.alg;
             sc = c.ips_scale;
+            div = c.lanes_div;
         }
-        const int d = default_ips(W);
+        lanes[b] = alg == SPMM_ALG_MERGE ? lanes_for(std::max(v[b].n, 1)) : lanes_of(v[b].n, div);
+        const int d = default_ips(lanes[b]);
         algs[b] = alg;
         ips[b] = sc > 0 ? d * 2 : sc < 0 ? std::max(4, d / 2) : d;
     }
     spmm_batched_plan* p = nullptr;
-    const int st = build_plan(v, algs, ips, s, &p);
+    const int st = build_plan(v, algs, ips, lanes, s, &p);
     if (st != SPMM_OK) return st;
     p->max_row = lmax;
     *plan = p;
@@ -581,7 +658,9 @@ int spmm_batched_capture_graph(spmm_batched_plan_t* plan, void* stream) {
 int spmm_batched_launch_graph(const spmm_batched_plan_t* plan, void* stream) {
     if (!plan || !plan->exec) return SPMM_ERR_INVALID_VALUE;
     const cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
-    if (e == cudaSuccess) g_launches.fetch_add((plan->n_items > 0) + (plan->total_tiles > 1), std::memory_order_relaxed);
+    if (e == cudaSuccess)
+        g_launches.fetch_add((plan->n_row_items > 0) + (plan->n_items > plan->n_row_items) + (plan->total_tiles > 1),
+                             std::memory_order_relaxed);
     return status_of(e);
 }
 
@@ -591,6 +670,7 @@ int spmm_batched_run_unfused(const spmm_batched_plan_t* plan, void* stream) {
         const auto& mt = plan->mats[b];
         spmm_tuning_t t{};
         t.items_per_subwarp = plan->ips[b];
+        t.lanes_per_row = plan->lanes[b];
         const int st = spmm_csr_ex(mt.m, mt.k, mt.n, mt.nnz, mt.row_ptr, mt.col_ind, mt.vals, SPMM_F32, mt.B, SPMM_F32,
                                    mt.ldb, mt.C, SPMM_F32, mt.ldc, plan->algs[b], &t, nullptr, 0, nullptr, stream);
         if (st != SPMM_OK) return st;

@@ -125,3 +125,31 @@ def test_batched_workload_full_size_sampled(gpu_lib):
                                                    oracle.abs_bound_rows(rows, a.row_ptr, a.col_ind, a.vals, B)))
     assert worst <= FP32_TOL
     plan.close()
+
+
+@pytest.mark.parametrize("policy", ["row_split", "merge", "autotune"])
+def test_batched_column_slabs(gpu_lib, policy):
+    """Matrices wider than one lane group (n = 256 and 384: 64 and 96 16-byte vectors, so two and
+    three column slabs of 32 lanes) next to narrow ones, in one plan: every slab's item writes its
+    own columns, and the merge slabs share the matrix's partition and carries."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(17)
+    host, dev = [], []
+    for i, n in enumerate((256, 32, 384, 64, 256)):
+        m = int(rng.integers(500, 3000))
+        lens = rng.poisson(12.0, m)
+        if i == 2:
+            lens[m // 2] = m  # a heavy row: the Type 1 guard sends this matrix to merge under "model"
+        a = gen.csr_from_lengths(np.minimum(lens, m), m, 60 + i)
+        B = gen.normal_matrix(a.k, n, 70 + i)
+        host.append((a, B))
+        dev.append(tuple(torch.from_numpy(x).cuda() for x in (a.row_ptr, a.col_ind, a.vals, B)) +
+                   (torch.full((a.m, n), float("nan"), device="cuda"),))
+    pol = {"row_split": pkg.BATCHED_ROW_SPLIT, "merge": pkg.BATCHED_MERGE, "autotune": pkg.BATCHED_AUTOTUNE}[policy]
+    plan = pkg.BatchedPlan(*[[d[i] for d in dev] for i in range(5)], policy=pol)
+    plan.run()
+    torch.cuda.synchronize()
+    check_all(host, dev)
+    plan.close()
