@@ -67,12 +67,17 @@ typedef enum {
                                than the row split on GB300 at every density
                                tried; no selector picks it               */
     SPMM_ALG_ROW_SPLIT_HYBRID = 5 /* row split whose granularity (Section 4.1)
-                               follows the row: rows of at most
-                               tuning->long_row_len nonzeros keep their lane
-                               group; longer rows (the Type 1 imbalance of
-                               Section 3.2) are queued on the device and cut
-                               into segments of a warp each, whose partial
-                               sums are added in segment order.  Needs a
+                               follows the row: a warp owns a block of
+                               consecutive rows, and its lane groups split
+                               the block's rows of at most
+                               tuning->long_row_len nonzeros into runs of
+                               equal nonzero count (no row is split; a batch
+                               of gathers may serve several rows, against
+                               the Type 2 imbalance of Section 3.2); longer
+                               rows (Type 1) are queued on the device and
+                               taken by one lane group, or cut into
+                               segments of a warp each whose partial sums
+                               are added in segment order.  Needs a
                                workspace (spmm_csr_workspace_size)       */
 } spmm_alg_t;
 
@@ -103,13 +108,16 @@ typedef struct {
     int items_per_subwarp;   /* merge based: merge-path items (rows + nonzeros) per
                                 lane group; a tile holds 256 / lanes_per_row groups     */
     int long_row_len;        /* SPMM_ALG_ROW_SPLIT_HYBRID: rows with more nonzeros than
-                                this are cut into warp segments; 0 selects 4 batches of
-                                the lane group (32 nonzeros for lane groups of <= 8
-                                lanes, 4 x lanes otherwise)                             */
+                                this leave the row-block pass (queued rows of up to 4x
+                                this are taken by one lane group, longer ones by warp
+                                segments); 0 selects max(32, lanes per row)            */
     double merge_threshold;  /* heuristic threshold on nnz / m; <= 0 selects 9.35       */
     long long max_row_len;   /* SPMM_ALG_AUTO_GB300: longest row of A when the caller
                                 knows it; 0 makes the call measure it on the device
                                 (a reduction and a 4-byte copy that synchronises)       */
+    int block_rows;          /* SPMM_ALG_ROW_SPLIT_HYBRID: consecutive rows per warp in
+                                the row-block pass, 1-256 (larger values act as 256);
+                                0 selects 128, or 64 for >= 16 lanes per row            */
 } spmm_tuning_t;
 
 /* Human-readable name of a status code (static storage). */

@@ -50,7 +50,8 @@ class SpmmTuning(ctypes.Structure):
 
     _fields_ = [("lanes_per_row", ctypes.c_int), ("column_slabs", ctypes.c_int),
                 ("items_per_subwarp", ctypes.c_int), ("long_row_len", ctypes.c_int),
-                ("merge_threshold", ctypes.c_double), ("max_row_len", ctypes.c_longlong)]
+                ("merge_threshold", ctypes.c_double), ("max_row_len", ctypes.c_longlong),
+                ("block_rows", ctypes.c_int)]
 
 
 _i, _ll, _vp, _sz, _d = ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double

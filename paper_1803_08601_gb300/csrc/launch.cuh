@@ -85,13 +85,15 @@ cudaError_t rowsplit_launch(const RowSplitArgs& a, const Shape& s, cudaStream_t 
     return s.vec == 1 ? rowsplit_launch_vec<TV, TB, TC, 1, SR>(a, s, st) : rowsplit_launch_vec<TV, TB, TC, V, SR>(a, s, st);
 }
 
-// Hybrid row split: zero the queue counters, then the row pass (grid as the
-// plain row split) and the segment pass, a persistent grid of one wave chained
-// behind the row pass with programmatic dependent launch.
+// Hybrid row split: zero the queue counters, then the row-block pass (a warp
+// per block of l.block_rows rows) and the segment pass, a persistent grid of
+// one wave chained behind it with programmatic dependent launch.
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>
 cudaError_t hybrid_launch_one(const RowSplitArgs& a, const LongRowArgs& l, const Shape& s, int sms, cudaStream_t st) {
-    const long long rows_per_cta = kThreads / W;
-    const long long gx = (a.m + rows_per_cta - 1) / rows_per_cta;
+    constexpr long long warps_per_cta = kThreads / 32;
+    if (l.block_rows < 1 || l.block_rows > kMaxBlockRows) return cudaErrorInvalidValue;
+    const long long blocks = ((long long)a.m + l.block_rows - 1) / l.block_rows;
+    const long long gx = (blocks + warps_per_cta - 1) / warps_per_cta;
     if (gx > 0x7fffffffLL || s.slabs > 65535 || s.slabs < 1) return cudaErrorInvalidConfiguration;
     auto seg_kern = rowsplit_segment_kernel<TV, TB, TC, VEC, W, SR>;
     static thread_local int cached_dev = -1;
@@ -100,21 +102,21 @@ cudaError_t hybrid_launch_one(const RowSplitArgs& a, const LongRowArgs& l, const
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev != cached_dev) {
-        int blocks = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, seg_kern, kThreads, 0);
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, seg_kern, kThreads, 0);
         if (e != cudaSuccess) return e;
         cached_dev = dev;
-        cached_blocks = blocks < 1 ? 1 : blocks;
+        cached_blocks = nb < 1 ? 1 : nb;
     }
-    e = cudaMemsetAsync(l.counts, 0, 3 * sizeof(int), st);
+    e = cudaMemsetAsync(l.counts, 0, 4 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    rowsplit_hybrid_kernel<TV, TB, TC, VEC, W, SR><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a, l);
+    rowsplit_block_kernel<TV, TB, TC, VEC, W, SR><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a, l);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    const long long warps_per_cta = kThreads / 32;
+    const long long max_items = (long long)l.max_singles + l.max_parts + (l.max_mid + 32 / W - 1) / (32 / W);
     long long sx = (long long)cached_blocks * std::max(sms, 1);
-    sx = std::min<long long>(sx, ((long long)(l.max_singles + l.max_parts) * s.slabs + warps_per_cta - 1) / warps_per_cta);
+    sx = std::min<long long>(sx, (max_items * s.slabs + warps_per_cta - 1) / warps_per_cta);
     if (sx < 1) sx = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)sx);

@@ -220,29 +220,41 @@ MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
 }
 
 // Hybrid row split (SPMM_ALG_ROW_SPLIT_HYBRID).  A lane group of W lanes
-// takes BS = max(W, kUnroll) nonzeros per batch; a row stays in the row pass
-// for at most 4 batches (long_len = 4 BS unless the caller sets it), and a
-// segment holds 16 warp batches (32 / W lane groups x BS nonzeros each).
+// takes BS = max(W, kUnroll) nonzeros per batch.  Rows of at most long_len
+// nonzeros stay in the row-block pass (long_len = max(32, BS) unless the
+// caller sets it), whose warps own 128 consecutive rows (64 for W >= 16);
+// queued rows of at most mid_len = 4 long_len go to one lane group each; a
+// warp segment holds 16 warp batches (32 / W lane groups x BS nonzeros each).
+// The defaults are the fastest of a sweep of long_len in {16, ..., 256} and
+// block_rows in {64, 128, 256} on a 1M x 1M power-law matrix, n = 8 to 128.
 struct HybridLayout {
-    int long_len, seg_len, max_singles, max_parts;
-    size_t off_counts, off_single, off_multi, off_arrive, off_partial, total;
+    int long_len, mid_len, seg_len, block_rows, max_mid, max_singles, max_parts;
+    size_t off_counts, off_mid, off_single, off_multi, off_arrive, off_partial, total;
 };
 
-HybridLayout hybrid_layout(long long nnz, int n, const Shape& s, int long_len_req) {
+HybridLayout hybrid_layout(int m, long long nnz, int n, const Shape& s, const spmm_tuning_t& t) {
     HybridLayout H{};
     const int bs = std::max(s.W, kUnroll);
-    H.long_len = long_len_req > 0 ? long_len_req : 4 * bs;
+    const long long def_long = std::max(32, bs);
+    const long long long_len = t.long_row_len > 0 ? t.long_row_len : def_long;
+    H.long_len = (int)std::min<long long>(long_len, 0x3fffffffLL);
+    H.mid_len = (int)std::min<long long>(4 * long_len, 0x7fffffffLL);
     H.seg_len = 16 * (32 / s.W) * bs;
-    // single rows: at most nnz / (long_len + 1) rows are longer than long_len; partial slots: a row of
-    // L > seg_len nonzeros takes at most ceil(L / seg_len) <= L / seg_len + 1 of them, and there are at
-    // most nnz / (seg_len + 1) such rows
-    const long long singles = nnz / ((long long)H.long_len + 1) + 1;
+    H.block_rows = t.block_rows > 0 ? std::min(t.block_rows, kMaxBlockRows) : (s.W >= 16 ? 64 : 128);
+    // mid rows: at most nnz / (long_len + 1) rows are longer than long_len; single rows: at most
+    // nnz / (mid_len + 1); partial slots: a row of L > seg_len nonzeros takes at most
+    // ceil(L / seg_len) <= L / seg_len + 1 of them, and there are at most nnz / (seg_len + 1) such rows
+    const long long mids = std::min<long long>(m, nnz / ((long long)H.long_len + 1) + 1);
+    const long long singles = std::min<long long>(m, nnz / ((long long)H.mid_len + 1) + 1);
     const long long parts = 2 * (nnz / H.seg_len) + 2;
+    H.max_mid = (int)std::min<long long>(mids, 0x7fffffffLL);
     H.max_singles = (int)std::min<long long>(singles, 0x7fffffffLL);
     H.max_parts = (int)std::min<long long>(parts, 0x7fffffffLL);
     size_t off = 0;
     H.off_counts = off;
-    off = align256(off + 3 * sizeof(int));
+    off = align256(off + 4 * sizeof(int));
+    H.off_mid = off;
+    off = align256(off + (size_t)H.max_mid * sizeof(int));
     H.off_single = off;
     off = align256(off + (size_t)H.max_singles * sizeof(int));
     H.off_multi = off;
@@ -457,7 +469,7 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
         return cuda_status(L->tiled(ta, shape, s));
     }
     if (a == SPMM_ALG_ROW_SPLIT_HYBRID) {
-        const HybridLayout H = hybrid_layout(nnz, n, shape, t_eff.long_row_len);
+        const HybridLayout H = hybrid_layout(m, nnz, n, shape, t_eff);
         bool own = false;
         unsigned char* ws = static_cast<unsigned char*>(workspace);
         if (!ws) {
@@ -473,10 +485,14 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
         RowSplitArgs ra{m, n, row_ptr, col_ind, vals, B, ldb, C, ldc};
         LongRowArgs la{};
         la.long_len = H.long_len;
+        la.mid_len = H.mid_len;
         la.seg_len = H.seg_len;
+        la.block_rows = H.block_rows;
+        la.max_mid = H.max_mid;
         la.max_singles = H.max_singles;
         la.max_parts = H.max_parts;
         la.counts = reinterpret_cast<int*>(ws + H.off_counts);
+        la.mid = reinterpret_cast<int*>(ws + H.off_mid);
         la.single = reinterpret_cast<int*>(ws + H.off_single);
         la.multi = reinterpret_cast<int2*>(ws + H.off_multi);
         la.arrive = reinterpret_cast<int*>(ws + H.off_arrive);
@@ -575,7 +591,7 @@ const char* spmm_status_string(int status) {
     }
 }
 
-int spmm_version(void) { return 100; }
+int spmm_version(void) { return 101; }
 
 long long spmm_launch_count(void) { return g_launches.load(); }
 
@@ -637,7 +653,7 @@ size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int 
                 if (slabs) t.column_slabs = slabs;
                 Shape s;
                 if (!shape_for(n, vec, &t, &s)) return 0;
-                best = std::max(best, hybrid_layout(nnz, n, s, t.long_row_len).total);
+                best = std::max(best, hybrid_layout(m, nnz, n, s, t).total);
             }
         }
         return best;

@@ -456,11 +456,13 @@ def test_host_entry_few_long_rows(gpu_lib):
 @pytest.mark.parametrize("n", [1, 8, 32, 64, 128, 300])
 @pytest.mark.parametrize("long_row_len", [1, 7, 64, 1000])
 def test_hybrid_integer_rows_across_the_threshold_are_bitwise(gpu_lib, n, long_row_len):
-    """Hybrid row split: rows just below, at and above the long-row threshold and
-    rows of many segments (up to 40,000 nonzeros, so with 512-nonzero segments
-    up to 79 partial sums added by the row's last warp) on integer data: every
-    partial sum is an exact integer, so the result must equal the oracle bit
-    for bit whichever rows the row pass keeps."""
+    """Hybrid row split: rows just below, at and above the long-row threshold,
+    rows taken by one lane group and rows of many segments (up to 40,000
+    nonzeros, so with 512-nonzero segments up to 79 partial sums added by the
+    row's last warp) on integer data, with blocks of 1, 37, 128 and 256 rows per
+    warp: every partial sum is an exact integer, so the result must equal the
+    oracle bit for bit whichever rows the row-block pass keeps and however a
+    block's rows are split among its lane groups."""
     import torch
 
     rng = np.random.default_rng(100 + n)
@@ -473,7 +475,9 @@ def test_hybrid_integer_rows_across_the_threshold_are_bitwise(gpu_lib, n, long_r
     B = rng.integers(-4, 5, size=(50_000, n)).astype(np.float32)
     ref = oracle.spmm(rp, ci, v, B).astype(np.float32)
     for tuning in (dict(long_row_len=long_row_len), dict(long_row_len=long_row_len, column_slabs=3),
-                   dict(long_row_len=long_row_len, lanes_per_row=1)):
+                   dict(long_row_len=long_row_len, lanes_per_row=1), dict(long_row_len=long_row_len, block_rows=1),
+                   dict(long_row_len=long_row_len, block_rows=37, lanes_per_row=2),
+                   dict(long_row_len=long_row_len, block_rows=256)):
         C = run(gpu_lib, torch, rp, ci, v, B, "hybrid", tuning=tuning)
         assert np.array_equal(C.cpu().numpy(), ref), tuning
 
