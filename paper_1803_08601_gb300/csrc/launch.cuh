@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "hybrid.cuh"
 #include "kernels.cuh"
 
 namespace spmm {
