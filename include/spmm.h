@@ -120,7 +120,8 @@ typedef struct {
                                 0 selects 128, or 64 for >= 16 lanes per row            */
 } spmm_tuning_t;
 
-/* Human-readable name of a status code (static storage). */
+/* Human-readable name of a status code (static storage).  The paper defines
+   no error reporting; the codes are this library's own. */
 const char *spmm_status_string(int status);
 
 /* Library ABI version (major * 100 + minor). */
@@ -177,8 +178,10 @@ int spmm_default_column_slabs(int alg, int k, int n, int b_type);
 
 /*
  * Longest row of A (max over i of row_ptr[i+1] - row_ptr[i]) computed on the
- * device and written to *max_row_len (host).  Synchronises `stream`.  Uses a
- * 4-byte stream-ordered device allocation.
+ * device and written to *max_row_len (host): the quantity behind the Type 1
+ * imbalance of Section 3.2, which spmm_select_alg_gb300 takes.  Synchronises
+ * `stream`.  The result words live in an 8-byte device buffer per host thread
+ * and device, allocated at the first call and kept until exit.
  */
 int spmm_csr_max_row_length(int m, const int *row_ptr, long long *max_row_len, void *stream);
 
@@ -194,8 +197,12 @@ int spmm_csr(int m, int k, int n, const int *row_ptr, const int *col_ind, const 
              const float *B, long long ldb, float *C, long long ldc, int alg, void *stream);
 
 /*
- * Full form.  nnz is the host copy of row_ptr[m] (pass -1 to have it read
- * back, which synchronises `stream`).  vals_type / b_type / c_type are
+ * Full form of C = A B (Section 1; the algorithms of Sections 4.1 and 4.2,
+ * chosen as in Section 5.4 for SPMM_ALG_AUTO).  Storage precision (16-bit
+ * vals, B and C with float32 accumulation), the workspace, the launch shape
+ * and the status word are this library's additions; the paper's kernels are
+ * float32 throughout.  nnz is the host copy of row_ptr[m] (pass -1 to have it
+ * read back, which synchronises `stream`).  vals_type / b_type / c_type are
  * spmm_dtype_t values; the supported combinations (vals, B, C) are
  * (f32,f32,f32), (bf16,bf16,bf16), (bf16,bf16,f32), (bf16,f16,f16),
  * (bf16,f16,f32), (f16,f16,f16) and (f16,f16,f32); others return
@@ -242,7 +249,11 @@ int spmm_csr_semiring(int m, int k, int n, long long nnz, const int *row_ptr, co
                       int *d_status, void *stream);
 
 /*
- * Bytes of workspace spmm_csr_ex needs for these sizes.  0 for row split.
+ * Bytes of workspace spmm_csr_ex needs for these sizes.  For the merge-based
+ * algorithm this holds the merge-path coordinates of every tile boundary
+ * (PARTITIONSPMM of Algorithm 1, Section 4.2) and each tile's carry-out and
+ * head partial rows that FIXCARRYOUT combines; for the hybrid row split, its
+ * queues of long rows and their segments' partial sums.  0 for row split.
  * alg SPMM_ALG_AUTO is resolved with the heuristic first.  Returns 0 for
  * invalid arguments.
  */
