@@ -214,6 +214,9 @@ int spmm_csr(int m, int k, int n, const int *row_ptr, const int *col_ind, const 
  * with tuning->lanes_per_row lanes per row (0: from the mean row length) and
  * the merge based with 4, 8 or 16 path items per thread
  * (tuning->items_per_subwarp; 0: 8).
+ * ldb times the size of B's element type must be below 2^32 bytes
+ * (SPMM_ERR_INVALID_VALUE otherwise): the kernels address rows of B with a
+ * 32-bit byte stride.
  * The workspace must not be used by another call that may run concurrently.
  * d_status: optional device int; a bounded wait that runs out stores
  * SPMM_ERR_TIMEOUT there (the caller clears it).

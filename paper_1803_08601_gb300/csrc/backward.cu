@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) sddmm_kernel(SddmmArgs a) {
             part[u] = 0.0f;
             if (p < p1) {
                 while (p >= row_end) row_end = __ldg(a.row_ptr + (++row) + 1);
-                const TD* brow = B + (long long)__ldg(a.col_ind + p) * a.ldb;
+                const TD* brow = row_at(B, __ldg(a.col_ind + p), (unsigned)(a.ldb * (long long)sizeof(TD)));
                 const TD* drow = dC + (long long)row * a.lddc;
                 for (int j = sl; j < nchunks; j += W) {
                     const Raw<TD, VEC> x = load_raw<TD, VEC>(brow + (long long)j * VEC);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) sddmm_warp_kernel(SddmmArgs a) {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 const int j = lane + 32 * c;
-                x[u][c] = (u < cnt && j < nchunks) ? load_raw<TD, VEC>(B + (long long)cols[u] * a.ldb + (long long)j * VEC)
+                x[u][c] = (u < cnt && j < nchunks) ? load_raw<TD, VEC>(row_at(B + (long long)j * VEC, cols[u], (unsigned)(a.ldb * (long long)sizeof(TD))))
                                                    : zero_raw<TD, VEC>();
             }
         float part[U];
@@ -580,6 +580,7 @@ int sddmm_csr(int m, int k, int n, long long nnz, const int* row_ptr, const int*
     if (!row_ptr || !col_ind || !out || m == 0 || k == 0) return SPMM_ERR_INVALID_VALUE;
     if (n > 0 && (!dC || !B || lddc < n || ldb < n)) return SPMM_ERR_INVALID_VALUE;
     if (dc_type != b_type) return SPMM_ERR_UNSUPPORTED;
+    if (ldb * (b_type == SPMM_F32 ? 4LL : 2LL) > 0xffffffffLL) return SPMM_ERR_INVALID_VALUE;  // rows of B < 4 GiB apart
     SddmmArgs a{m, n, nnz, row_ptr, col_ind, dC, lddc, B, ldb, out, 32};
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) {  // empty dot products

@@ -514,6 +514,7 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
         if (mt.m > 0 && mt.n > 0) {
             if (!mt.row_ptr || !mt.C || mt.ldc < mt.n || (mt.nnz > 0 && (!mt.col_ind || !mt.vals || !mt.B || mt.ldb < mt.n)))
                 return SPMM_ERR_INVALID_VALUE;
+            if (mt.ldb > 0xffffffffLL / 4) return SPMM_ERR_INVALID_VALUE;  // rows of B < 4 GiB apart
             // the batched kernel uses 16-byte accesses only
             if (mt.n % 4 || mt.ldb % 4 || mt.ldc % 4 || ((uintptr_t)mt.B % 16) || ((uintptr_t)mt.C % 16))
                 return SPMM_ERR_UNSUPPORTED;

@@ -99,6 +99,16 @@ __device__ __forceinline__ Raw<T, VEC> zero_raw() {
     return r;
 }
 
+// Row r of a row-major matrix whose rows are stride_bytes apart, from the
+// address of row 0 (offset to the caller's columns).  A 32-bit row index times
+// a 32-bit byte stride is one wide multiply-add per gather, where a 64-bit
+// index product costs several instructions on the path every nonzero takes;
+// the host entry points reject leading dimensions of 2^32 bytes or more.
+template <typename T>
+__device__ __forceinline__ const T* row_at(const T* base, int r, unsigned stride_bytes) {
+    return reinterpret_cast<const T*>(reinterpret_cast<const char*>(base) + (unsigned long long)(unsigned)r * stride_bytes);
+}
+
 // acc[e] += a * element e of r, in float32 (fused multiply-add).
 template <typename T, int VEC>
 __device__ __forceinline__ void fma_raw(float (&acc)[VEC], float a, const Raw<T, VEC>& r) {

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
                 const int j = g * U + u;
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
                     const int j = g * U + u;
                     const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                     vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                    bv[u] = (in(j) && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0)
+                    bv[u] = (in(j) && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB))))
                                               : zero_raw<TB, VEC>();
                 }
 #pragma unroll

@@ -93,7 +93,7 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
                 const int j = g * U + u;  // nonzero j of the batch sits in lane j % W, slot j / W
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -380,7 +380,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
                 const int j = g * U + u;
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(B + (long long)c * a.ldb + col0) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -632,11 +632,11 @@ __global__ void __launch_bounds__(kThreads) spmv_rowsplit_kernel(RowSplitArgs a)
                 v[u] = load_f(vals + p + u * G);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = load_f(x + (long long)c[u] * a.ldb);
+            for (int u = 0; u < 4; ++u) b[u] = load_f(row_at(x, c[u], (unsigned)(a.ldb * (long long)sizeof(TB))));
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc = SR::mul_add(acc, v[u], b[u]);
         }
-        for (; p < re; p += G) acc = SR::mul_add(acc, load_f(vals + p), load_f(x + (long long)__ldg(col + p) * a.ldb));
+        for (; p < re; p += G) acc = SR::mul_add(acc, load_f(vals + p), load_f(row_at(x, __ldg(col + p), (unsigned)(a.ldb * (long long)sizeof(TB)))));
     }
     if constexpr (G > 1) {
 #pragma unroll
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) spmv_merge_kernel(MergeArgs a) {
         }
 #pragma unroll
         for (int u = 0; u < T; ++u)
-            b[u] = tid + u * kThreads < nz ? load_f(x + (long long)c[u] * a.ldb) : 0.0f;
+            b[u] = tid + u * kThreads < nz ? load_f(row_at(x, c[u], (unsigned)(a.ldb * (long long)sizeof(TB)))) : 0.0f;
 #pragma unroll
         for (int u = 0; u < T; ++u) {
             const int i = tid + u * kThreads;

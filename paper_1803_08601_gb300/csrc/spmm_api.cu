@@ -446,6 +446,7 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
              int* d_status, void* stream) {
     int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
     if (st != SPMM_OK) return st;
+    if (ldb * (long long)dtype_size(b_type) > 0xffffffffLL) return SPMM_ERR_INVALID_VALUE;  // rows of B < 4 GiB apart
     if (!L) return SPMM_ERR_UNSUPPORTED;
     if (m == 0 || n == 0) return SPMM_OK;
     cudaStream_t s = (cudaStream_t)stream;

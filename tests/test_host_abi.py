@@ -102,6 +102,8 @@ def test_argument_checks_return_before_any_device_work(lib):
     assert call(m=-1) == pkg.ERR_INVALID_VALUE
     assert call(n=-3) == pkg.ERR_INVALID_VALUE
     assert call(ldb=3) == pkg.ERR_INVALID_VALUE
+    assert call(ldb=1 << 30) == pkg.ERR_INVALID_VALUE  # float32 rows of B 2^32 bytes apart
+    assert call(ldb=1 << 31, b_type=pkg.BF16, vals_type=pkg.BF16, c_type=pkg.BF16) == pkg.ERR_INVALID_VALUE
     assert call(ldc=2) == pkg.ERR_INVALID_VALUE
     assert call(alg=7) == pkg.ERR_INVALID_VALUE
     assert call(alg=6) == pkg.ERR_INVALID_VALUE
