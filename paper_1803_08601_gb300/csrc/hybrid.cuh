@@ -247,12 +247,18 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
                 bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
             }
+            if (__all_sync(kFullMask, !skip && p + min(cnt, (g + 1) * U) <= rend)) {  // no row ends here
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = g * U + u;
-                if (j < cnt) {
-                    while (p + j >= rend && row < ib) next_row();  // rows (empty or queued too) ending before it
-                    if (!skip) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+                for (int u = 0; u < U; ++u)
+                    if (g * U + u < cnt) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = g * U + u;
+                    if (j < cnt) {
+                        while (p + j >= rend && row < ib) next_row();  // rows (empty or queued too) ending before it
+                        if (!skip) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+                    }
                 }
             }
         }

@@ -382,13 +382,21 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
                 bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
             }
+            // no row of any lane group ends among these U nonzeros (the common case inside the long
+            // rows of a skewed matrix): accumulate without the per-nonzero row-end checks
+            if (__all_sync(kFullMask, base + min(cnt, (g + 1) * U) <= rend)) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = g * U + u;
-                if (j < cnt) {
-                    const int p = base + j;
-                    while (p >= rend) emit();  // rows (possibly empty) that end before nonzero p
-                    accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+                for (int u = 0; u < U; ++u)
+                    if (g * U + u < cnt) accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = g * U + u;
+                    if (j < cnt) {
+                        const int p = base + j;
+                        while (p >= rend) emit();  // rows (possibly empty) that end before nonzero p
+                        accum_raw<SR, TB, VEC>(acc, vv[u], bv[u]);
+                    }
                 }
             }
         }
