@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) sddmm_kernel(SddmmArgs a) {
             part[u] = 0.0f;
             if (p < p1) {
                 while (p >= row_end) row_end = __ldg(a.row_ptr + (++row) + 1);
-                const TD* brow = row_at(B, __ldg(a.col_ind + p), (unsigned)(a.ldb * (long long)sizeof(TD)));
+                const TD* brow = gather_row(B, 0, __ldg(a.col_ind + p), a.ldb);
                 const TD* drow = dC + (long long)row * a.lddc;
                 for (int j = sl; j < nchunks; j += W) {
                     const Raw<TD, VEC> x = load_raw<TD, VEC>(brow + (long long)j * VEC);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) sddmm_warp_kernel(SddmmArgs a) {
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 const int j = lane + 32 * c;
-                x[u][c] = (u < cnt && j < nchunks) ? load_raw<TD, VEC>(row_at(B + (long long)j * VEC, cols[u], (unsigned)(a.ldb * (long long)sizeof(TD))))
+                x[u][c] = (u < cnt && j < nchunks) ? load_raw<TD, VEC>(gather_row(B, (long long)j * VEC, cols[u], a.ldb))
                                                    : zero_raw<TD, VEC>();
             }
         float part[U];

@@ -109,6 +109,17 @@ __device__ __forceinline__ const T* row_at(const T* base, int r, unsigned stride
     return reinterpret_cast<const T*>(reinterpret_cast<const char*>(base) + (unsigned long long)(unsigned)r * stride_bytes);
 }
 
+// The gathered row r of B at column offset col0 with leading dimension ld.
+// float32 rows take the byte-stride form above.  For 16-bit rows the compiler
+// then keeps fewer of a batch's gathers in flight (the row split of bf16 rows
+// of 256 bytes: 2.06 -> 2.51 ms on a 2M x 2M, 32 per row matrix), so they keep
+// the 64-bit index product.
+template <typename T>
+__device__ __forceinline__ const T* gather_row(const T* B, long long col0, int r, long long ld) {
+    if constexpr (sizeof(T) == 4) return row_at(B + col0, r, (unsigned)(ld * (long long)sizeof(T)));
+    else return B + (long long)r * ld + col0;
+}
+
 // acc[e] += a * element e of r, in float32 (fused multiply-add).
 template <typename T, int VEC>
 __device__ __forceinline__ void fma_raw(float (&acc)[VEC], float a, const Raw<T, VEC>& r) {

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
                 const int j = g * U + u;
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(gather_row(B, col0, c, a.ldb)) : zero_raw<TB, VEC>();
             }
             if (__all_sync(kFullMask, !skip && p + min(cnt, (g + 1) * U) <= rend)) {  // no row ends here
 #pragma unroll
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
                     const int j = g * U + u;
                     const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                     vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                    bv[u] = (in(j) && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB))))
+                    bv[u] = (in(j) && col_ok) ? load_raw<TB, VEC>(gather_row(B, col0, c, a.ldb))
                                               : zero_raw<TB, VEC>();
                 }
 #pragma unroll

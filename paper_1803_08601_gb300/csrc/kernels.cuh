@@ -93,7 +93,7 @@ __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long ro
                 const int j = g * U + u;  // nonzero j of the batch sits in lane j % W, slot j / W
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(gather_row(B, col0, c, a.ldb)) : zero_raw<TB, VEC>();
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -380,7 +380,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<T
                 const int j = g * U + u;
                 const int c = __shfl_sync(kFullMask, mc[j / W], j % W, W);
                 vv[u] = __shfl_sync(kFullMask, mv[j / W], j % W, W);
-                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(row_at(B + col0, c, (unsigned)(a.ldb * (long long)sizeof(TB)))) : zero_raw<TB, VEC>();
+                bv[u] = (j < cnt && col_ok) ? load_raw<TB, VEC>(gather_row(B, col0, c, a.ldb)) : zero_raw<TB, VEC>();
             }
             // no row of any lane group ends among these U nonzeros (the common case inside the long
             // rows of a skewed matrix): accumulate without the per-nonzero row-end checks
@@ -640,11 +640,11 @@ __global__ void __launch_bounds__(kThreads) spmv_rowsplit_kernel(RowSplitArgs a)
                 v[u] = load_f(vals + p + u * G);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = load_f(row_at(x, c[u], (unsigned)(a.ldb * (long long)sizeof(TB))));
+            for (int u = 0; u < 4; ++u) b[u] = load_f(gather_row(x, 0, c[u], a.ldb));
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc = SR::mul_add(acc, v[u], b[u]);
         }
-        for (; p < re; p += G) acc = SR::mul_add(acc, load_f(vals + p), load_f(row_at(x, __ldg(col + p), (unsigned)(a.ldb * (long long)sizeof(TB)))));
+        for (; p < re; p += G) acc = SR::mul_add(acc, load_f(vals + p), load_f(gather_row(x, 0, __ldg(col + p), a.ldb)));
     }
     if constexpr (G > 1) {
 #pragma unroll
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) spmv_merge_kernel(MergeArgs a) {
         }
 #pragma unroll
         for (int u = 0; u < T; ++u)
-            b[u] = tid + u * kThreads < nz ? load_f(row_at(x, c[u], (unsigned)(a.ldb * (long long)sizeof(TB)))) : 0.0f;
+            b[u] = tid + u * kThreads < nz ? load_f(gather_row(x, 0, c[u], a.ldb)) : 0.0f;
 #pragma unroll
         for (int u = 0; u < T; ++u) {
             const int i = tid + u * kThreads;
