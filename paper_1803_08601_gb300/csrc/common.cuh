@@ -20,6 +20,11 @@ constexpr int kThreads = 256;       // threads per CTA of the row-split, SDDMM a
 __host__ __device__ constexpr int merge_cta_threads(int W) { return W >= 16 ? 256 : 128; }
 __host__ __device__ constexpr int merge_tile_items(int W) { return W >= 16 ? 2048 : 1024; }
 constexpr int kUnroll = 8;     // gathers of B in flight per lane
+// Gathers in flight per lane for accesses of VEC elements of T: kUnroll for one
+// 16-byte vector, half as many for the two 16-byte vectors of the float32
+// access of 8 columns (so a lane keeps 128 bytes in flight either way).
+template <typename T, int VEC>
+__host__ __device__ constexpr int gathers_per_batch() { return VEC * (int)sizeof(T) > 16 ? kUnroll / 2 : kUnroll; }
 
 // ------------------------------------------------------------------ element types
 
@@ -57,9 +62,12 @@ __device__ __forceinline__ void load_vec(const T* p, float (&out)[VEC]) {
     if constexpr (VEC == 1) {
         out[0] = load_f(p);
     } else if constexpr (sizeof(T) == 4) {
-        static_assert(VEC == 4, "float vectors are 4 wide");
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+        static_assert(VEC == 4 || VEC == 8, "float accesses are one or two 16-byte vectors");
+#pragma unroll
+        for (int i = 0; i < VEC; i += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p + i));
+            out[i] = v.x; out[i + 1] = v.y; out[i + 2] = v.z; out[i + 3] = v.w;
+        }
     } else {
         static_assert(VEC == 8, "16-bit vectors are 8 wide");
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
@@ -78,14 +86,21 @@ __device__ __forceinline__ void load_vec(const T* p, float (&out)[VEC]) {
 template <typename T, int VEC> struct Raw;
 template <typename T> struct Raw<T, 1> { T v; };
 template <> struct Raw<float, 4> { float4 v; };
+template <> struct Raw<float, 8> { float4 v, w; };  // two 16-byte vectors of one lane
 template <> struct Raw<__nv_bfloat16, 8> { uint4 v; };
 template <> struct Raw<__half, 8> { uint4 v; };
 
 template <typename T, int VEC>
 __device__ __forceinline__ Raw<T, VEC> load_raw(const T* p) {
     Raw<T, VEC> r;
-    if constexpr (VEC == 1) r.v = __ldg(p);
-    else if constexpr (sizeof(T) == 4) r.v = __ldg(reinterpret_cast<const float4*>(p));
+    if constexpr (VEC == 1) {
+        r.v = __ldg(p);
+    } else if constexpr (sizeof(T) == 4 && VEC == 8) {
+        r.v = __ldg(reinterpret_cast<const float4*>(p));
+        r.w = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    } else if constexpr (sizeof(T) == 4) {
+        r.v = __ldg(reinterpret_cast<const float4*>(p));
+    }
     else r.v = __ldg(reinterpret_cast<const uint4*>(p));
     return r;
 }
@@ -93,8 +108,14 @@ __device__ __forceinline__ Raw<T, VEC> load_raw(const T* p) {
 template <typename T, int VEC>
 __device__ __forceinline__ Raw<T, VEC> zero_raw() {
     Raw<T, VEC> r;
-    if constexpr (VEC == 1) r.v = Elem<T>::from_f(0.0f);
-    else if constexpr (sizeof(T) == 4) r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (VEC == 1) {
+        r.v = Elem<T>::from_f(0.0f);
+    } else if constexpr (sizeof(T) == 4 && VEC == 8) {
+        r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.w = r.v;
+    } else if constexpr (sizeof(T) == 4) {
+        r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     else r.v = make_uint4(0u, 0u, 0u, 0u);
     return r;
 }
@@ -125,6 +146,15 @@ template <typename T, int VEC>
 __device__ __forceinline__ void fma_raw(float (&acc)[VEC], float a, const Raw<T, VEC>& r) {
     if constexpr (VEC == 1) {
         acc[0] = fmaf(a, Elem<T>::to_f(r.v), acc[0]);
+    } else if constexpr (sizeof(T) == 4 && VEC == 8) {
+        acc[0] = fmaf(a, r.v.x, acc[0]);
+        acc[1] = fmaf(a, r.v.y, acc[1]);
+        acc[2] = fmaf(a, r.v.z, acc[2]);
+        acc[3] = fmaf(a, r.v.w, acc[3]);
+        acc[4] = fmaf(a, r.w.x, acc[4]);
+        acc[5] = fmaf(a, r.w.y, acc[5]);
+        acc[6] = fmaf(a, r.w.z, acc[6]);
+        acc[7] = fmaf(a, r.w.w, acc[7]);
     } else if constexpr (sizeof(T) == 4) {
         acc[0] = fmaf(a, r.v.x, acc[0]);
         acc[1] = fmaf(a, r.v.y, acc[1]);
@@ -254,8 +284,14 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename T, int VEC>
 __device__ __forceinline__ Raw<T, VEC> lds_raw(const T* p) {
     Raw<T, VEC> r;
-    if constexpr (VEC == 1) r.v = *p;
-    else if constexpr (sizeof(T) == 4) r.v = *reinterpret_cast<const float4*>(p);
+    if constexpr (VEC == 1) {
+        r.v = *p;
+    } else if constexpr (sizeof(T) == 4 && VEC == 8) {
+        r.v = *reinterpret_cast<const float4*>(p);
+        r.w = *(reinterpret_cast<const float4*>(p) + 1);
+    } else if constexpr (sizeof(T) == 4) {
+        r.v = *reinterpret_cast<const float4*>(p);
+    }
     else r.v = *reinterpret_cast<const uint4*>(p);
     return r;
 }

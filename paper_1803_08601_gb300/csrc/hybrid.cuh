@@ -81,7 +81,7 @@ template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = P
 __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) rowsplit_block_kernel(RowSplitArgs a,
                                                                                                    LongRowArgs l) {
     pdl_launch_dependents();
-    constexpr int U = kUnroll;
+    constexpr int U = gathers_per_batch<TB, VEC>();
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
     constexpr int BS = W * CV;               // nonzeros per batch
     constexpr int G = BS / U;                // groups of U gathers per batch
@@ -317,7 +317,7 @@ __device__ __forceinline__ void finish_long_row(const float* __restrict__ part, 
 // loaded while the current batch's gathers are in flight.
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitArgs a, LongRowArgs l, int slabs) {
-    constexpr int U = kUnroll;
+    constexpr int U = gathers_per_batch<TB, VEC>();
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per warp batch
     constexpr int BS = W * CV;               // nonzeros per lane group per warp batch
     constexpr int G = BS / U;                // groups of U gathers per batch

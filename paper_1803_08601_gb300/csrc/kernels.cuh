@@ -49,7 +49,7 @@ struct RowSplitArgs {
 // same number of times.
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR = PlusTimes>
 __device__ __forceinline__ void rowsplit_row(const RowSplitArgs& a, long long row, int slab) {
-    constexpr int U = kUnroll;
+    constexpr int U = gathers_per_batch<TB, VEC>();
     constexpr int CV = (U > W) ? U / W : 1;  // (column, value) pairs per lane per batch
     constexpr int BS = W * CV;               // nonzeros per batch
     constexpr int G = BS / U;                // groups of U gathers per batch
@@ -297,7 +297,7 @@ __device__ __forceinline__ void merge_load_plain(const MergeArgs& a, const Merge
 template <typename TV, typename TB, typename TC, int VEC, int W, int NT, typename SR = PlusTimes>
 __device__ __forceinline__ void merge_tile(const MergeArgs& a, const MergeView<TV, VEC, W, NT>& v, int item, int b) {
     using L = MergeSmem<TV, VEC, W, NT>;
-    constexpr int U = kUnroll;
+    constexpr int U = gathers_per_batch<TB, VEC>();
     constexpr int CV = (U > W) ? U / W : 1;
     constexpr int BS = W * CV;
     constexpr int G = BS / U;

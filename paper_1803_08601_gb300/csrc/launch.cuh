@@ -147,11 +147,16 @@ cudaError_t hybrid_launch_vec(const RowSplitArgs& a, const LongRowArgs& l, const
     }
 }
 
+// vec: 1, the 16-byte width of TB, or for float32 B also 8 (two 16-byte
+// vectors per lane).
 template <typename TV, typename TB, typename TC, typename SR>
 cudaError_t hybrid_launch(const RowSplitArgs& a, const LongRowArgs& l, const Shape& s, int sms, cudaStream_t st) {
     constexpr int V = Elem<TB>::kVec;
-    return s.vec == 1 ? hybrid_launch_vec<TV, TB, TC, 1, SR>(a, l, s, sms, st)
-                      : hybrid_launch_vec<TV, TB, TC, V, SR>(a, l, s, sms, st);
+    if (s.vec == 1) return hybrid_launch_vec<TV, TB, TC, 1, SR>(a, l, s, sms, st);
+    if constexpr (sizeof(TB) == 4) {
+        if (s.vec == 8) return hybrid_launch_vec<TV, TB, TC, 8, SR>(a, l, s, sms, st);
+    }
+    return hybrid_launch_vec<TV, TB, TC, V, SR>(a, l, s, sms, st);
 }
 
 template <typename TV, typename TB, typename TC, int VEC, int W, typename SR>

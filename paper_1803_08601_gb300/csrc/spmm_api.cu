@@ -170,6 +170,14 @@ bool choose_shape(int n, int tb, int tc, const void* B, long long ldb, const voi
     return shape_for(n, vec_ok ? V : 1, t, s);
 }
 
+// The hybrid row split reads float32 rows of B as two 16-byte vectors per
+// lane (8 columns, half as many gathers in flight) once rows hold 32 columns
+// or more: on a 1M x 1M power-law matrix, n = 32 / 64 / 128, 0.354 / 0.644 /
+// 1.217 -> 0.319 / 0.584 / 1.129 ms; at n = 8 one vector per lane stays faster.
+bool hybrid_two_vectors(int n, int b_type, long long ldb, long long ldc, const Shape& s) {
+    return b_type == SPMM_F32 && s.vec == 4 && n >= 32 && n % 8 == 0 && ldb % 8 == 0 && ldc % 8 == 0;
+}
+
 // Column slabs when B is much larger than L2 and its rows are wide: each pass
 // then gathers half of every row, over a B slab twice as likely to be found in
 // L2 (measured on GB300: merge with 512-byte rows and row split with >= 256-byte
@@ -464,6 +472,8 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
     spmm_tuning_t t_eff = tuning ? *tuning : spmm_tuning_t{};
     if (t_eff.column_slabs <= 0 && t_eff.lanes_per_row <= 0) t_eff.column_slabs = default_slabs(a, k, n, b_type);
     if (!choose_shape(n, b_type, c_type, B, ldb, C, ldc, &t_eff, &shape)) return SPMM_ERR_INVALID_VALUE;
+    if (a == SPMM_ALG_ROW_SPLIT_HYBRID && hybrid_two_vectors(n, b_type, ldb, ldc, shape) && !shape_for(n, 8, &t_eff, &shape))
+        return SPMM_ERR_INVALID_VALUE;
     const bool spmv = n == 1;  // y = A x: the SpMV forms of both families
     if (a == SPMM_ALG_TILED && shape.vec > 1 && !spmv) {
         TiledArgs ta{m, n, k, row_ptr, col_ind, vals, B, ldb, C, ldc, d_status};
@@ -647,7 +657,7 @@ size_t spmm_csr_workspace_size(int m, int k, int n, long long nnz, int alg, int 
     if (alg == SPMM_ALG_ROW_SPLIT_HYBRID) {
         if (m == 0 || n == 0) return 0;
         size_t best = 0;
-        for (int vec : {1, 16 / dtype_size(b_type)}) {
+        for (int vec : {1, 16 / dtype_size(b_type), 8}) {
             for (int slabs : {0, 2}) {
                 spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
                 if (slabs && (t.column_slabs > 0 || t.lanes_per_row > 0)) continue;
