@@ -997,11 +997,12 @@ def run_sweep(args):
             v = torch.rand(total, device=dev, generator=torch.Generator(device=dev).manual_seed(lg)) * 2 - 1
             B = torch.randn(k, n, device=dev, generator=torch.Generator(device=dev).manual_seed(100 + lg))
             C = torch.empty(m, n, device=dev)
-            ws = torch.empty(pkg.workspace_size(m, k, n, total, "merge"), dtype=torch.uint8, device=dev)
+            ws = torch.empty(max(pkg.workspace_size(m, k, n, total, "merge"),
+                                 pkg.workspace_size(m, k, n, total, "hybrid")), dtype=torch.uint8, device=dev)
             row = {"sweep": "aspect", "m": m, "k": k, "nnz": total, "n": n,
                    "paper_pick": name[pkg.spmm_select_alg(m, total, 0.0)],
                    "gb300_pick": name[pkg.spmm_select_alg_gb300(m, total, k, n, pkg.F32)]}
-            for alg in ("row_split", "merge"):
+            for alg in ("row_split", "merge", "hybrid"):
                 r = reps if (alg == "merge" or k <= (1 << 16)) else 1  # very long rows: one timed run
                 t = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=total, workspace=ws),
                           flush, stream, r)
@@ -1102,10 +1103,11 @@ def run_gather_sweep(pkg, torch, dev, flush, stream, reps):
 
 
 def run_selector_sweep(pkg, torch, dev, flush, stream, reps):
-    """Both families on 1M x 1M matrices of three row-length families (every row the same length,
-    Poisson lengths, power-law lengths with density exponent 2 capped at 10^5) and mean lengths
-    2-64, at n = 8, 32, 64, 128; each point records the two times, the Section 5.4 rule's pick,
-    the GB300 selector's pick and each pick's time relative to the faster family (1 = right)."""
+    """Row split, merge and the hybrid row split on 1M x 1M matrices of three row-length families
+    (every row the same length, Poisson lengths, power-law lengths with density exponent 2 capped
+    at 10^5) and mean lengths 2-64, at n = 8, 32, 64, 128; each point records the three times, the
+    Section 5.4 rule's pick, the GB300 selector's pick and each pick's time relative to the fastest
+    of the three (1 = right)."""
     name = ALG_NAME
     m = k = 1_000_000
     Bs = {n: torch.randn(k, n, device=dev, generator=torch.Generator(device=dev).manual_seed(300 + n))
@@ -1127,9 +1129,10 @@ def run_selector_sweep(pkg, torch, dev, flush, stream, reps):
             del a
             for n, B in Bs.items():
                 C = torch.empty(m, n, device=dev)
-                ws = torch.empty(max(256, pkg.workspace_size(m, k, n, nnz, "merge")), dtype=torch.uint8, device=dev)
+                ws = torch.empty(max(256, pkg.workspace_size(m, k, n, nnz, "merge"),
+                                     pkg.workspace_size(m, k, n, nnz, "hybrid")), dtype=torch.uint8, device=dev)
                 t = {}
-                for alg in ("row_split", "merge"):
+                for alg in ("row_split", "merge", "hybrid"):
                     r = 1 if (alg == "row_split" and lmax > 20_000) else reps
                     t[alg] = _time(torch, lambda: pkg.spmm(rp, ci, v, B, alg=alg, out=C, nnz=nnz, workspace=ws), flush,
                                    stream, r)
@@ -1138,6 +1141,7 @@ def run_selector_sweep(pkg, torch, dev, flush, stream, reps):
                 gb300 = name[pkg.spmm_select_alg_gb300(m, nnz, lmax, n, pkg.F32)]
                 print(json.dumps({"sweep": "selector", "family": family, "mean_row": nnz / m, "max_row": lmax,
                                   "n": n, "nnz": nnz, "row_split_ms": t["row_split"], "merge_ms": t["merge"],
+                                  "hybrid_ms": t["hybrid"],
                                   "paper_pick": paper, "paper_regret": t[paper] / best,
                                   "gb300_pick": gb300, "gb300_regret": t[gb300] / best}), flush=True)
                 del C, ws

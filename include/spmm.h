@@ -140,20 +140,25 @@ long long spmm_launch_count(void);
 int spmm_select_alg(int m, long long nnz, double threshold);
 
 /*
- * GB300 selector (SPMM_ALG_AUTO_GB300), pure host function.  When the
- * longest row is long enough to be the critical path of row split (Type 1
- * imbalance, Section 3.2: max_row_len > 1024 and max_row_len * 8192 > nnz,
- * fitted on a GB300 sweep of dense-as-CSR matrices from 2 x 2^23 to
- * 2^23 x 2) it returns SPMM_ALG_ROW_SPLIT_HYBRID for rows of B under 64
- * bytes (n * element size of B) and SPMM_ALG_MERGE otherwise (measured on
- * the 10^6 x 10^6 power-law matrix: the hybrid is ahead at 32-byte rows,
- * merge from 128-byte rows on).  Otherwise it returns SPMM_ALG_MERGE when a
- * row of B is at least 64 bytes and the mean row length d = nnz / m is below
- * a threshold T: T = 7 for rows of B of 256 bytes or more, T = 3 for 64-255
- * bytes, and 2T when the longest row is at least 2d (uneven rows); measured
- * crossovers of the two kernels on GB300 for uniform and Poisson row lengths
- * (the paper's single 9.35 was measured on a K40c); and SPMM_ALG_ROW_SPLIT
- * otherwise.  m == 0 returns row split.
+ * GB300 selector (SPMM_ALG_AUTO_GB300), pure host function, fitted on GB300
+ * sweeps of the three families (float32 B; the paper's single 9.35 was
+ * measured on a K40c).  With row bytes = n * element size of B and
+ * d = nnz / m:
+ *   - when the longest row is long enough to be the critical path of row split
+ *     (Type 1 imbalance, Section 3.2: max_row_len > 1024 and
+ *     max_row_len * 8192 >= nnz, fitted on dense-as-CSR matrices from
+ *     2 x 2^23 to 2^23 x 2): SPMM_ALG_ROW_SPLIT_HYBRID for rows of B of up to
+ *     128 bytes, SPMM_ALG_MERGE for wider ones (on 10^6 x 10^6 power-law
+ *     matrices the hybrid is ahead at 32- and 128-byte rows, merge from 256);
+ *   - rows of B under 64 bytes: SPMM_ALG_ROW_SPLIT;
+ *   - d < 3: SPMM_ALG_ROW_SPLIT_HYBRID (its lane groups pack runs of short
+ *     rows), or SPMM_ALG_MERGE for rows of B of 512 bytes or more when the
+ *     longest row is at least 2d (uneven rows);
+ *   - rows of B under 256 bytes: SPMM_ALG_ROW_SPLIT;
+ *   - SPMM_ALG_MERGE when d < T, T = 8 for uneven rows, else 5 for rows of B
+ *     of 512 bytes or more and 3 for 256-511 bytes; SPMM_ALG_ROW_SPLIT
+ *     otherwise (measured crossovers for uniform and Poisson row lengths).
+ * m == 0 returns row split.
  */
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type);
 

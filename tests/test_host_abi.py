@@ -54,33 +54,36 @@ def test_heuristic_matches_oracle(lib, m, nnz):
 
 def test_gb300_selector(lib):
     F, H = pkg.F32, pkg.BF16
-    # Type 1 guard: a very long row sends a matrix with a long mean row length to merge, or to the
-    # hybrid row split when rows of B are under 64 bytes
+    # Type 1 guard: a very long row sends the matrix to the hybrid row split for rows of B of up
+    # to 128 bytes, to merge for wider ones
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 64, F) == pkg.ALG_MERGE
-    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 32, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 32, F) == pkg.ALG_ROW_SPLIT_HYBRID
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 8, F) == pkg.ALG_ROW_SPLIT_HYBRID
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 100_000, 16, H) == pkg.ALG_ROW_SPLIT_HYBRID
     assert pkg.spmm_select_alg_gb300(1_000_000, 15_821_532, 1_000, 64, F) == pkg.ALG_ROW_SPLIT
     assert pkg.spmm_select_alg_gb300(4096, 65_536, 16, 64, F) == pkg.ALG_ROW_SPLIT
-    # the aspect-ratio sweep's boundary: 4096 rows of 4096 go to merge, 8192 rows of 2048 to row split
+    # the aspect-ratio sweep's boundary: 8192 rows of 2048 (8192 * 2048 = nnz) still go to merge,
+    # 16384 rows of 1024 to the row split
     assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 64, F) == pkg.ALG_MERGE
-    assert pkg.spmm_select_alg_gb300(8192, 1 << 24, 2048, 64, F) == pkg.ALG_ROW_SPLIT
-    # mean-length rule (points of the row-length family sweep, 1M x 1M): never merge below 64-byte
-    # rows of B; threshold 7 for rows of 256 bytes or more, 3 for 64-255 bytes; doubled for uneven rows
+    assert pkg.spmm_select_alg_gb300(8192, 1 << 24, 2048, 64, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(16384, 1 << 24, 1024, 64, F) == pkg.ALG_ROW_SPLIT
+    # mean-length rules (points of the row-length family sweep, 1M x 1M)
     M = 10**6
-    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 8, F) == pkg.ALG_ROW_SPLIT        # 32-byte rows
-    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 32, F) == pkg.ALG_MERGE           # uniform, 128 B
-    assert pkg.spmm_select_alg_gb300(M, 4 * M, 4, 32, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 32, H) == pkg.ALG_MERGE           # 64-byte bf16 rows
-    assert pkg.spmm_select_alg_gb300(M, 6 * M, 6, 64, F) == pkg.ALG_MERGE           # uniform, 256 B
-    assert pkg.spmm_select_alg_gb300(M, 8 * M, 8, 64, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(M, 6 * M, 6, 128, F) == pkg.ALG_MERGE
-    assert pkg.spmm_select_alg_gb300(M, 8 * M, 8, 128, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(M, 4 * M, 16, 32, F) == pkg.ALG_MERGE          # Poisson-like, 128 B
-    assert pkg.spmm_select_alg_gb300(M, 8 * M, 24, 32, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(M, 12 * M, 33, 64, F) == pkg.ALG_MERGE         # Poisson-like, 256 B
-    assert pkg.spmm_select_alg_gb300(M, 16 * M, 40, 64, F) == pkg.ALG_ROW_SPLIT
-    assert pkg.spmm_select_alg_gb300(M, 32 * M, 61, 128, F) == pkg.ALG_ROW_SPLIT    # longest < 2 x mean
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 8, F) == pkg.ALG_ROW_SPLIT          # 32-byte rows
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 32, F) == pkg.ALG_ROW_SPLIT_HYBRID  # d < 3
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 128, F) == pkg.ALG_ROW_SPLIT_HYBRID
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 13, 64, F) == pkg.ALG_ROW_SPLIT_HYBRID  # Poisson-like
+    assert pkg.spmm_select_alg_gb300(M, 2 * M, 13, 128, F) == pkg.ALG_MERGE           # uneven, 512 B
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 4, 32, F) == pkg.ALG_ROW_SPLIT         # 128 B: row split
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 16, 32, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 4, 64, F) == pkg.ALG_ROW_SPLIT         # uniform, 256 B: T = 3
+    assert pkg.spmm_select_alg_gb300(M, 4 * M, 4, 128, F) == pkg.ALG_MERGE            # uniform, 512 B: T = 5
+    assert pkg.spmm_select_alg_gb300(M, 6 * M, 6, 128, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 6 * M, 20, 64, F) == pkg.ALG_MERGE            # uneven: T = 8
+    assert pkg.spmm_select_alg_gb300(M, 8 * M, 24, 64, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 6 * M, 20, 128, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(M, 12 * M, 33, 128, F) == pkg.ALG_ROW_SPLIT
+    assert pkg.spmm_select_alg_gb300(M, 32 * M, 61, 128, F) == pkg.ALG_ROW_SPLIT      # longest < 2 x mean
     assert pkg.spmm_select_alg_gb300(0, 0, 0, 64, F) == pkg.ALG_ROW_SPLIT
 
 
