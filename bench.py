@@ -983,7 +983,7 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4 + 1024, device=dev)
     reps = max(3, min(args.steps, 5))
-    n = 64
+    n = args.n[0] if args.n else 64  # width of the aspect-ratio and density sweeps
     name = ALG_NAME
     if args.sweep == "gather":
         return run_gather_sweep(pkg, torch, dev, flush, stream, reps)

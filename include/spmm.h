@@ -147,9 +147,12 @@ int spmm_select_alg(int m, long long nnz, double threshold);
  *   - when the longest row is long enough to be the critical path of row split
  *     (Type 1 imbalance, Section 3.2: max_row_len > 1024 and
  *     max_row_len * 8192 >= nnz, fitted on dense-as-CSR matrices from
- *     2 x 2^23 to 2^23 x 2): SPMM_ALG_ROW_SPLIT_HYBRID for rows of B of up to
- *     128 bytes, SPMM_ALG_MERGE for wider ones (on 10^6 x 10^6 power-law
- *     matrices the hybrid is ahead at 32- and 128-byte rows, merge from 256);
+ *     2 x 2^23 to 2^23 x 2): SPMM_ALG_ROW_SPLIT_HYBRID when rows of B are at
+ *     most 128 bytes and the longest row is at least 16 d (most rows short
+ *     beside the long ones: on 10^6 x 10^6 power-law matrices the hybrid is
+ *     ahead at 32- and 128-byte rows, merge from 256), else SPMM_ALG_MERGE
+ *     (rows all long: merge's equal tiles win);
+ *   - d >= 768 with rows of B under 256 bytes: SPMM_ALG_MERGE;
  *   - rows of B under 64 bytes: SPMM_ALG_ROW_SPLIT;
  *   - d < 3: SPMM_ALG_ROW_SPLIT_HYBRID (its lane groups pack runs of short
  *     rows), or SPMM_ALG_MERGE for rows of B of 512 bytes or more when the

@@ -616,16 +616,22 @@ int spmm_select_alg(int m, long long nnz, double threshold) {
 int spmm_select_alg_gb300(int m, long long nnz, long long max_row_len, int n, int b_type) {
     if (m <= 0) return SPMM_ALG_ROW_SPLIT;
     const long long row_bytes = (long long)n * (dtype_size(b_type) ? dtype_size(b_type) : 4);
-    if (max_row_len > 1024 && max_row_len * 8192 >= nnz)  // Type 1 guard
-        return row_bytes <= 128 ? SPMM_ALG_ROW_SPLIT_HYBRID : SPMM_ALG_MERGE;
+    const double d = (double)nnz / (double)m;
+    const bool uneven = (double)max_row_len >= 2.0 * d;
+    // Type 1 guard: the hybrid when most rows are short beside the long ones (the longest at least
+    // 16 times the mean) and rows of B are at most 128 bytes, else merge (rows all long: merge's
+    // equal tiles beat the hybrid's warp segments)
+    if (max_row_len > 1024 && max_row_len * 8192 >= nnz)
+        return (row_bytes <= 128 && (double)max_row_len >= 16.0 * d) ? SPMM_ALG_ROW_SPLIT_HYBRID : SPMM_ALG_MERGE;
+    // rows of 768 or more nonzeros with rows of B under 256 bytes: a lane group of the row split
+    // waits on its row, merge spreads it over tiles
+    if (row_bytes < 256 && d >= 768.0) return SPMM_ALG_MERGE;
     if (row_bytes < 64) return SPMM_ALG_ROW_SPLIT;
     // mean-length rules measured on GB300 (uniform and Poisson rows, 1M x 1M, float32): below 3
     // nonzeros per row the hybrid's packed runs of short rows win (merge for uneven rows of 512-byte
     // rows of B); from 3 on the row split wins for rows of B under 256 bytes, and for wider rows
     // merge wins below 3 (256 bytes) or 5 (512 bytes and more), or below 8 when the longest row is at
     // least twice the mean (uneven rows cost the row split more than the merge path)
-    const double d = (double)nnz / (double)m;
-    const bool uneven = (double)max_row_len >= 2.0 * d;
     if (d < 3.0) return (row_bytes >= 512 && uneven) ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT_HYBRID;
     if (row_bytes < 256) return SPMM_ALG_ROW_SPLIT;
     const double threshold = uneven ? 8.0 : (row_bytes >= 512 ? 5.0 : 3.0);

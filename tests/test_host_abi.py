@@ -67,6 +67,13 @@ def test_gb300_selector(lib):
     assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 64, F) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg_gb300(8192, 1 << 24, 2048, 64, F) == pkg.ALG_MERGE
     assert pkg.spmm_select_alg_gb300(16384, 1 << 24, 1024, 64, F) == pkg.ALG_ROW_SPLIT
+    # rows all long (longest under 16 x mean) stay with merge at narrow rows of B too
+    assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 8, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(4096, 1 << 24, 4096, 32, F) == pkg.ALG_MERGE
+    # rows of 768 or more nonzeros with rows of B under 256 bytes: merge
+    assert pkg.spmm_select_alg_gb300(16384, 1 << 24, 1024, 8, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(16384, 1 << 24, 1024, 32, F) == pkg.ALG_MERGE
+    assert pkg.spmm_select_alg_gb300(32768, 1 << 24, 512, 32, F) == pkg.ALG_ROW_SPLIT
     # mean-length rules (points of the row-length family sweep, 1M x 1M)
     M = 10**6
     assert pkg.spmm_select_alg_gb300(M, 2 * M, 2, 8, F) == pkg.ALG_ROW_SPLIT          # 32-byte rows
