@@ -5,7 +5,7 @@ exponent 2, mean about 16, capped at 100,000, 1% empty rows) times row-major
 float32 B of widths n = 8, 32, 64, 128.  One step = C = A B for every width,
 each through the C ABI with the algorithm chosen by the GB300 selector (the
 Section 5.4 mean-row-length rule recalibrated, plus a longest-row guard); the
-JSON line also reports the Section 5.4 rule's own pick and both families'
+JSON line also reports the Section 5.4 rule's own pick and each family's
 times (``--alg`` overrides).  After the headline, the growth forms are
 measured: 16-bit storage (2M x 2M, n = 128), a GCN layer's forward and
 backward (500k nodes, n = 256, with the transpose on its own) and a
@@ -15,9 +15,10 @@ synthetic and seeded (gen/).
 Timing: inputs resident in HBM; L2 is flushed (a write of twice its size)
 before every step, outside the events; each call is bracketed by CUDA events on
 the launching stream.  ``e2e`` times the same step through
-``spmm_csr_host_async`` (host buffers; H2D of A and B, D2H of C and the final
-stream synchronisation inside the timed region; the synchronous
-``spmm_csr_host`` beside it) next to the host link's own copy rates.  ``--impl reference`` times the FP64 CPU oracle on
+``spmm_csr_host_multi`` (host buffers; H2D of A once and of every B, D2H of
+every C and the final stream synchronisation inside the timed region; one
+``spmm_csr_host_async`` or synchronous ``spmm_csr_host`` call per width
+beside it) next to the host link's own copy rates.  ``--impl reference`` times the FP64 CPU oracle on
 a bounded row sample.  ``--sweep aspect|density|spmv|tiling|selector`` runs one
 of the parameter sweeps instead (a JSON line per point), and ``--ingest-ncu``
 turns the recorded ncu traffic capture into the JSON the roofline reads.
@@ -595,49 +596,67 @@ def breakdown(pkg, torch, one, ns, nnz, comp, steps, flush, stream):
 
 
 def e2e(pkg, torch, a, ns, Bs, args, tuning):
-    """The step through the host-buffer entry: pinned host A, B in; host C out; copies timed.
-    The step's products are queued with spmm_csr_host_async and the step ends with one
-    synchronisation of the stream (each product's uploads overlap the previous product's last
-    downloads); the same step through the synchronous spmm_csr_host is reported beside it."""
+    """The step through the host-buffer entries: pinned host A, B in; host C out; copies timed.
+    The step is one spmm_csr_host_multi call (A goes up once for the step's four products) and
+    one synchronisation of the stream.  Beside it: the same step as one spmm_csr_host_async call
+    per width (A goes up with each), and as synchronous spmm_csr_host calls."""
     rp = torch.from_numpy(a.row_ptr).pin_memory()
     ci = torch.from_numpy(a.col_ind).pin_memory()
     v = torch.from_numpy(a.vals).pin_memory()
     hB = {n: torch.from_numpy(Bs[n]).pin_memory() for n in ns}
     hC = {n: torch.empty((a.m, n), dtype=torch.float32).pin_memory() for n in ns}
-    h2d = sum((a.m + 1) * 4 + a.nnz * 8 + a.k * n * 4 for n in ns)
+    a_bytes = (a.m + 1) * 4 + a.nnz * 8
+    h2d = a_bytes + sum(a.k * n * 4 for n in ns)
+    h2d_per_width = sum(a_bytes + a.k * n * 4 for n in ns)
     d2h = sum(a.m * n * 4 for n in ns)
     stream = torch.cuda.current_stream()
     reps = max(5, min(args.steps, 10))
+    Bl, Cl = [hB[n] for n in ns], [hC[n] for n in ns]
 
-    def timed(wait):
-        for _ in range(max(args.warmup, 3)):  # warm-up steps (the staging pool grows to its steady size)
+    def step(mode):
+        if mode == "multi":
+            pkg.spmm_host_multi(rp, ci, v, Bl, Cl, alg=args.alg, tuning=tuning)
+        else:
             for n in ns:
-                pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning, wait=wait)
-            stream.synchronize()
+                pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning, wait=mode == "sync")
+        stream.synchronize()
+
+    def timed(mode):
+        for _ in range(max(args.warmup, 3)):  # warm-up steps (the staging pool grows to its steady size)
+            step(mode)
         steps_s = []
         gc.disable()  # a collection of Python objects inside a step is not the library's time
         try:
             for _ in range(reps):  # each step is timed on its own, the median reported
                 t0 = time.perf_counter()
-                for n in ns:
-                    pkg.spmm_host(rp, ci, v, hB[n], hC[n], alg=args.alg, tuning=tuning, wait=wait)
-                stream.synchronize()
+                step(mode)
                 steps_s.append(time.perf_counter() - t0)
         finally:
             gc.enable()
         return steps_s
 
-    sync_s = timed(True)
-    steps_s = timed(False)
+    sync_s = timed("sync")
+    async_s = timed("async")
+    steps_s = timed("multi")
     t = statistics.median(steps_s)
     flops = sum(2.0 * a.nnz * n for n in ns)
     link = host_link(torch)
-    bound_ms = (h2d + d2h) / (link["duplex_gbs"] * 1e9) * 1e3
+
+    def bound(up, down):  # the copies alone at the measured one-way and duplex rates
+        return max(up / (link["h2d_gbs"] * 1e9), down / (link["d2h_gbs"] * 1e9),
+                   (up + down) / (link["duplex_gbs"] * 1e9)) * 1e3
+
+    bound_ms = bound(h2d, d2h)
+    t_async = statistics.median(async_s)
     return {"value": flops / t / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3, "step_ms": {"median": t * 1e3, "min": min(steps_s) * 1e3,
                                                 "max": max(steps_s) * 1e3, "steps": reps,
                                                 "all": [round(x * 1e3, 3) for x in steps_s]},
-            "api": "spmm_csr_host_async",
+            "api": "spmm_csr_host_multi",
+            "per_width_calls": {"api": "spmm_csr_host_async", "h2d_bytes_per_step": h2d_per_width,
+                                "ms_per_step": t_async * 1e3, "min": min(async_s) * 1e3, "max": max(async_s) * 1e3,
+                                "value": flops / t_async / 1e9,
+                                "frac_of_link_bound": bound(h2d_per_width, d2h) / (t_async * 1e3)},
             "sync_calls": {"api": "spmm_csr_host", "ms_per_step": statistics.median(sync_s) * 1e3,
                            "min": min(sync_s) * 1e3, "max": max(sync_s) * 1e3,
                            "value": flops / statistics.median(sync_s) / 1e9},

@@ -324,6 +324,30 @@ int spmm_csr_host_async(int m, int k, int n, const int *row_ptr, const int *col_
                         long long ldc, int alg, const spmm_tuning_t *tuning, void *stream);
 
 /*
+ * Several host-buffer products with one sparse matrix (no counterpart in the
+ * paper): C[i] = A B[i] for i < count, where B[i] is k x n[i] (leading
+ * dimension ldb[i]) and C[i] is m x n[i] (ldc[i]), all in HOST memory, with
+ * one vals / B / C type combination for all.  A goes up to the device once
+ * for all of them, which is the saving over count calls of
+ * spmm_csr_host_async.  The products run in the caller's order on the same
+ * pipeline of column slabs and row chunks of A (a narrow product first lets
+ * computing start soonest), and each block of every C[i] comes down as soon
+ * as it is computed.  alg and tuning apply to every product; with
+ * SPMM_ALG_AUTO_GB300 each product is selected for its own n[i] (the longest
+ * row is found once).  Queued like spmm_csr_host_async, with the same rules:
+ * the host inputs are read from call time on and must stay valid and
+ * unmodified until `stream` has been synchronised (or an event recorded on
+ * it after the call has completed), when every C[i] holds its result.
+ * Products with n[i] == 0 are skipped.  n, B, ldb, C and ldc are host arrays
+ * of count entries (they may be NULL when count == 0).  Argument errors of
+ * any product return before any work is queued.
+ */
+int spmm_csr_host_multi(int m, int k, const int *row_ptr, const int *col_ind, const void *vals, int vals_type,
+                        int count, const int *n, const void *const *B, int b_type, const long long *ldb,
+                        void *const *C, int c_type, const long long *ldc, int alg, const spmm_tuning_t *tuning,
+                        void *stream);
+
+/*
  * Self-test of the bounded device-side wait used by the merge kernel's
  * shared-memory staging: one CTA waits on an mbarrier phase that nothing
  * completes, for at most limit_ns nanoseconds of device time (clamped to

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "spmm_merge_partition": ([_i, _ll, _vp, _i, _i, _vp, _vp], _i),
     "spmm_csr_host": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
     "spmm_csr_host_async": ([_i, _i, _i, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp], _i),
+    "spmm_csr_host_multi": ([_i, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _i, _vp, _i, _TP, _vp], _i),
     "spmm_debug_bounded_wait": ([_vp, _ll, _vp], _i),
     "spmm_csr_noalloc": ([_i, _i, _i, _ll, _vp, _vp, _vp, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _TP, _vp, _vp], _i),
     "spmm_csr_static_scratch_bytes": ([], _sz),
@@ -194,6 +195,14 @@ def spmm_csr_host_async(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, l
                         stream) -> int:
     return load().spmm_csr_host_async(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc,
                                       alg, _tuning_ptr(tuning), stream)
+
+
+def spmm_csr_host_multi(m, k, row_ptr, col_ind, vals, vals_type, count, n, B, b_type, ldb, C, c_type, ldc, alg,
+                        tuning, stream) -> int:
+    """n, B, ldb, C, ldc: addresses of host arrays of count entries (int32, pointers, int64,
+    pointers, int64)."""
+    return load().spmm_csr_host_multi(m, k, row_ptr, col_ind, vals, vals_type, count, n, B, b_type, ldb, C, c_type,
+                                      ldc, alg, _tuning_ptr(tuning), stream)
 
 
 def spmm_debug_bounded_wait(d_status, limit_ns, stream) -> int:
@@ -377,6 +386,39 @@ def spmm_host(row_ptr, col_ind, vals, B, C, alg="auto", tuning=None, stream=None
             alg_code(alg), tuning, _stream_handle(stream))
     _check(st, name)
     return C
+
+
+def spmm_host_multi(row_ptr, col_ind, vals, Bs, Cs, alg="auto", tuning=None, stream=None):
+    """C_i = A @ B_i for every pair of host tensors (CPU, ideally pinned) in Bs, Cs, queued through
+    ``spmm_csr_host_multi``: A goes up once for all products.  The call returns once the work is
+    queued; every C_i is filled when ``stream`` (default: torch's current stream) has been
+    synchronised, and the operands must stay alive and A, B_i unchanged until then.  All B_i share
+    one dtype, all C_i another."""
+    tensors = [row_ptr, col_ind, vals, *Bs, *Cs]
+    if any(t.is_cuda for t in tensors):
+        raise ValueError("spmm_host_multi takes host tensors")
+    if len(Bs) != len(Cs):
+        raise ValueError("spmm_host_multi needs one C per B")
+    if any(B.dtype != Bs[0].dtype for B in Bs) or any(C.dtype != Cs[0].dtype for C in Cs):
+        raise ValueError("spmm_host_multi takes one B dtype and one C dtype")
+    count = len(Bs)
+    m = row_ptr.numel() - 1
+    k = Bs[0].shape[0] if count else 0
+    if any(B.shape[0] != k for B in Bs) or any(C.shape[0] != m or C.shape[1] != B.shape[1] for B, C in zip(Bs, Cs)):
+        raise ValueError("spmm_host_multi: shapes do not match")
+    n = (ctypes.c_int * max(count, 1))(*[B.shape[1] for B in Bs])
+    bp = (ctypes.c_void_p * max(count, 1))(*[B.data_ptr() for B in Bs])
+    ldb = (ctypes.c_longlong * max(count, 1))(*[B.stride(0) for B in Bs])
+    cp = (ctypes.c_void_p * max(count, 1))(*[C.data_ptr() for C in Cs])
+    ldc = (ctypes.c_longlong * max(count, 1))(*[C.stride(0) for C in Cs])
+    b_type = dtype_code(Bs[0].dtype) if count else F32
+    c_type = dtype_code(Cs[0].dtype) if count else F32
+    st = spmm_csr_host_multi(m, k, row_ptr.data_ptr(), col_ind.data_ptr(), vals.data_ptr(), dtype_code(vals.dtype),
+                             count, ctypes.addressof(n), ctypes.addressof(bp), b_type, ctypes.addressof(ldb),
+                             ctypes.addressof(cp), c_type, ctypes.addressof(ldc), alg_code(alg), tuning,
+                             _stream_handle(stream))
+    _check(st, "spmm_csr_host_multi")
+    return Cs
 
 
 def workspace_size(m, k, n, nnz, alg="auto", b_dtype=None, tuning=None) -> int:

@@ -741,44 +741,65 @@ int spmm_csr(int m, int k, int n, const int* row_ptr, const int* col_ind, const 
                        nullptr, nullptr, 0, nullptr, stream);
 }
 
-// The host-buffer product, enqueued on `stream` and the two copy streams; with `wait` the call
-// returns only when C is in host memory.
-static int host_product(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
-                        const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
-                        const spmm_tuning_t* tuning, void* stream, bool wait) {
-    if (m < 0 || k < 0 || n < 0) return SPMM_ERR_INVALID_VALUE;
+// The host-buffer products C_i = A B_i (i < count), enqueued on `stream` and the two copy streams:
+// A goes up once for all of them.  With `wait` the call returns only when every C_i is in host
+// memory.
+static int host_products(int m, int k, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                         int count, const int* n_of, const void* const* B_of, int b_type, const long long* ldb_of,
+                         void* const* C_of, int c_type, const long long* ldc_of, int alg_req,
+                         const spmm_tuning_t* tuning, void* stream, bool wait) {
+    if (m < 0 || k < 0 || count < 0) return SPMM_ERR_INVALID_VALUE;
+    if (count > 0 && (!n_of || !B_of || !ldb_of || !C_of || !ldc_of)) return SPMM_ERR_INVALID_VALUE;
     if (m > 0 && !row_ptr) return SPMM_ERR_INVALID_VALUE;
+    if (count == 0) return SPMM_OK;  // no products: the types name nothing
     const long long nnz = m > 0 ? row_ptr[m] : 0;
-    int st = check_args(m, k, n, nnz, row_ptr, col_ind, vals, B, ldb, C, ldc, alg);
-    if (st != SPMM_OK) return st;
+    for (int i = 0; i < count; ++i) {
+        const int st = check_args(m, k, n_of[i], nnz, row_ptr, col_ind, vals, B_of[i], ldb_of[i], C_of[i], ldc_of[i],
+                                  alg_req);
+        if (st != SPMM_OK) return st;
+    }
     const int sv = dtype_size(vals_type), sb = dtype_size(b_type), sc = dtype_size(c_type);
     if (!find_launchers(vals_type, b_type, c_type)) return SPMM_ERR_UNSUPPORTED;
-    if (m == 0 || n == 0) return SPMM_OK;
+    std::vector<int> prods;  // the products with work to do
+    for (int i = 0; i < count; ++i)
+        if (n_of[i] > 0) prods.push_back(i);
+    if (m == 0 || prods.empty()) return SPMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     keep_pool_memory();
     cudaStream_t up = nullptr, down = nullptr;
     if (!copy_streams(&up, &down)) return SPMM_ERR_CUDA;
 
-    // The algorithm is chosen once, for the whole matrix.
+    // The algorithm is chosen once per product, for the whole matrix (the longest row once for all).
     spmm_tuning_t t = tuning ? *tuning : spmm_tuning_t{};
-    if (alg == SPMM_ALG_AUTO_GB300) {
-        if (t.max_row_len <= 0)
-            for (int i = 0; i < m; ++i) t.max_row_len = std::max<long long>(t.max_row_len, row_ptr[i + 1] - row_ptr[i]);
-        alg = spmm_select_alg_gb300(m, nnz, t.max_row_len, n, b_type);
-    }
-    alg = resolve_alg(alg, m, nnz, &t);
+    if (alg_req == SPMM_ALG_AUTO_GB300 && t.max_row_len <= 0)
+        for (int i = 0; i < m; ++i) t.max_row_len = std::max<long long>(t.max_row_len, row_ptr[i + 1] - row_ptr[i]);
 
-    // Pipeline over the full-duplex host link.  Column slabs of B and C (at least 128 bytes of a
-    // row each) let slab j be computed while slab j+1 of B goes up and slab j-1 of C comes down;
-    // row chunks of A (equal shares of rows + nonzeros) let the first slab start as soon as the
-    // first chunk of A is on the device instead of all of A.  Order on the upload stream:
-    // B slab 0, A chunk 0 .. R-1, B slab 1 .. S-1.
+    // Pipeline over the full-duplex host link.  Column slabs of each B_i and C_i (at least 128
+    // bytes of a row each) let slab j be computed while slab j+1 of B goes up and slab j-1 of C
+    // comes down; row chunks of A (equal shares of rows + nonzeros) let the first slab start as
+    // soon as the first chunk of A is on the device instead of all of A.  Order on the upload
+    // stream, products in the caller's order: B_0 slab 0, A chunk 0 .. R-1, the other slabs of
+    // B_0, then B_1, B_2, ... in turn (putting the widest product first, measured on the power-law
+    // step of n = 8, 32, 64, 128, delays the first compute behind a large B slab: 7.39 -> 7.58 ms).
     const long long vb = 16 / sb, vc = 16 / sc;
-    const long long ldb_d = (n + vb - 1) / vb * vb, ldc_d = (n + vc - 1) / vc * vc;
-    int slabs = (int)std::min<long long>(4, std::max<long long>(1, (long long)n * sb / 128));
-    long long w = (n + slabs - 1) / slabs;
-    w = (w + 15) / 16 * 16;  // whole 16-byte vectors for every element size
-    slabs = (int)((n + w - 1) / w);
+    struct Prod {
+        int n, alg, slabs;
+        long long w, ldb_d, ldc_d;
+        size_t off_B, off_C;
+    };
+    std::vector<Prod> P(prods.size());
+    for (size_t q = 0; q < prods.size(); ++q) {
+        Prod& p = P[q];
+        p.n = n_of[prods[q]];
+        p.alg = alg_req == SPMM_ALG_AUTO_GB300 ? spmm_select_alg_gb300(m, nnz, t.max_row_len, p.n, b_type) : alg_req;
+        p.alg = resolve_alg(p.alg, m, nnz, &t);
+        p.ldb_d = (p.n + vb - 1) / vb * vb;
+        p.ldc_d = (p.n + vc - 1) / vc * vc;
+        int slabs = (int)std::min<long long>(4, std::max<long long>(1, (long long)p.n * sb / 128));
+        long long w = (p.n + slabs - 1) / slabs;
+        p.w = (w + 15) / 16 * 16;  // whole 16-byte vectors for every element size
+        p.slabs = (int)((p.n + p.w - 1) / p.w);
+    }
     const long long a_bytes = (long long)(m + 1) * 4 + nnz * (4 + sv);
     const int chunks = (int)std::max<long long>(1, std::min<long long>({4, m, a_bytes / (8LL << 20)}));
     std::vector<int> r(chunks + 1);  // chunk c holds rows [r[c], r[c+1])
@@ -807,21 +828,37 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
         off_val[c] = total;
         total += align256((size_t)cnnz * sv);
     }
-    // one merge workspace, lent to every block's call in turn (they run in order on `stream`)
+    // one workspace, lent to every block's call in turn (they run in order on `stream`)
     size_t ws_need = 0;
-    if (alg == SPMM_ALG_MERGE || alg == SPMM_ALG_ROW_SPLIT_HYBRID)
-        for (int c = 0; c < chunks; ++c)
-            for (int j = 0; j < slabs; ++j) {
-                const long long cw = std::min<long long>(w, n - j * w);
-                ws_need = std::max(ws_need, spmm_csr_workspace_size(r[c + 1] - r[c], k, (int)cw,
-                                                                    row_ptr[r[c + 1]] - row_ptr[r[c]], alg, b_type, &t));
-            }
-    const size_t off_B = total, off_C = off_B + align256((size_t)k * ldb_d * sb);
-    const size_t off_ws = off_C + align256((size_t)m * ldc_d * sc);
+    for (Prod& p : P) {
+        if (p.alg == SPMM_ALG_MERGE || p.alg == SPMM_ALG_ROW_SPLIT_HYBRID)
+            for (int c = 0; c < chunks; ++c)
+                for (int j = 0; j < p.slabs; ++j) {
+                    const long long cw = std::min<long long>(p.w, p.n - j * p.w);
+                    ws_need = std::max(ws_need, spmm_csr_workspace_size(r[c + 1] - r[c], k, (int)cw,
+                                                                        row_ptr[r[c + 1]] - row_ptr[r[c]], p.alg,
+                                                                        b_type, &t));
+                }
+        p.off_B = total;
+        total += align256((size_t)k * p.ldb_d * sb);
+        p.off_C = total;
+        total += align256((size_t)m * p.ldc_d * sc);
+    }
+    const size_t off_ws = total;
     total = off_ws + align256(ws_need);
     cudaMemPool_t pool = host_staging_pool();
     if (!pool) return SPMM_ERR_CUDA;
-    std::vector<cudaEvent_t> ev(4 + chunks + slabs + (size_t)slabs * chunks, nullptr);
+    // events: [0] uploads done, [1] compute done, [2] downloads + free done, [3] inputs ready,
+    // then A chunk c uploaded, then per product: slab j of B uploaded, block (j, c) of C computed
+    std::vector<size_t> ev_b(P.size()), ev_c(P.size());
+    size_t nev = 4 + chunks;
+    for (size_t q = 0; q < P.size(); ++q) {
+        ev_b[q] = nev;
+        nev += P[q].slabs;
+        ev_c[q] = nev;
+        nev += (size_t)P[q].slabs * chunks;
+    }
+    std::vector<cudaEvent_t> ev(nev, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
@@ -834,12 +871,11 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
         return cuda_status(e);
     }
     // The synchronous entry orders its uploads after the work already queued on `stream` (which may
-    // write the host inputs); the asynchronous entry reads them from call time on, so that its uploads
-    // can overlap the previous call's downloads.
+    // write the host inputs); the asynchronous entries read them from call time on, so that their
+    // uploads can overlap the previous call's downloads.
     if (wait) {
-        cudaEvent_t e_in = ev[3 + chunks + slabs + (size_t)slabs * chunks];
-        e = cudaEventRecord(e_in, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(up, e_in, 0);
+        e = cudaEventRecord(ev[3], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(up, ev[3], 0);
         if (e != cudaSuccess) {
             destroy_events();
             return cuda_status(e);
@@ -854,24 +890,25 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
         return SPMM_ERR_ALLOC;
     }
     unsigned char* base = static_cast<unsigned char*>(mem);
-    unsigned char* d_B = base + off_B;
-    unsigned char* d_C = base + off_C;
-    cudaEvent_t e_up = ev[0], e_s = ev[1], e_end = ev[2];  // uploads, compute, downloads + free done
-    cudaEvent_t* e_a = ev.data() + 3;                  // chunk c of A uploaded
-    cudaEvent_t* e_b = ev.data() + 3 + chunks;         // slab j of B uploaded
-    cudaEvent_t* e_c = ev.data() + 3 + chunks + slabs;  // block (j, c) of C computed
-    auto upload_b = [&](int j) {
-        const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
+    cudaEvent_t e_up = ev[0], e_s = ev[1], e_end = ev[2];
+    cudaEvent_t* e_a = ev.data() + 4;
+    auto upload_b = [&](size_t q, int j) {
+        const Prod& p = P[q];
+        const void* Bh = B_of[prods[q]];
+        const long long ldb = ldb_of[prods[q]];
+        const long long c0 = j * p.w, cw = std::min<long long>(p.w, p.n - c0);
+        unsigned char* d_B = base + p.off_B;
         cudaError_t x = cudaSuccess;
         if (k > 0 && nnz > 0)
-            x = (slabs == 1 && ldb == ldb_d)
-                    ? cudaMemcpyAsync(d_B, B, (size_t)k * ldb_d * sb, cudaMemcpyHostToDevice, up)
-                    : cudaMemcpy2DAsync(d_B + c0 * sb, (size_t)ldb_d * sb, static_cast<const unsigned char*>(B) + c0 * sb,
-                                        (size_t)ldb * sb, (size_t)cw * sb, (size_t)k, cudaMemcpyHostToDevice, up);
-        if (x == cudaSuccess) x = cudaEventRecord(e_b[j], up);
+            x = (p.slabs == 1 && ldb == p.ldb_d)
+                    ? cudaMemcpyAsync(d_B, Bh, (size_t)k * p.ldb_d * sb, cudaMemcpyHostToDevice, up)
+                    : cudaMemcpy2DAsync(d_B + c0 * sb, (size_t)p.ldb_d * sb,
+                                        static_cast<const unsigned char*>(Bh) + c0 * sb, (size_t)ldb * sb,
+                                        (size_t)cw * sb, (size_t)k, cudaMemcpyHostToDevice, up);
+        if (x == cudaSuccess) x = cudaEventRecord(ev[ev_b[q] + j], up);
         return x;
     };
-    e = upload_b(0);
+    e = upload_b(0, 0);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         const long long p0 = row_ptr[r[c]], p1 = row_ptr[r[c + 1]];
         e = cudaMemcpyAsync(base + off_rp[c], row_ptr + r[c], (size_t)(r[c + 1] - r[c] + 1) * 4, cudaMemcpyHostToDevice,
@@ -883,40 +920,49 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
                                 (size_t)(p1 - p0) * sv, cudaMemcpyHostToDevice, up);
         if (e == cudaSuccess) e = cudaEventRecord(e_a[c], up);
     }
-    for (int j = 1; j < slabs && e == cudaSuccess; ++j) e = upload_b(j);
-    if (e != cudaSuccess) st = cuda_status(e);
+    for (size_t q = 0; q < P.size() && e == cudaSuccess; ++q)
+        for (int j = q == 0 ? 1 : 0; j < P[q].slabs && e == cudaSuccess; ++j) e = upload_b(q, j);
+    int st = e == cudaSuccess ? SPMM_OK : cuda_status(e);
 
-    for (int j = 0; j < slabs && st == SPMM_OK; ++j) {
-        const long long c0 = j * w, cw = std::min<long long>(w, n - c0);
-        st = cuda_status(cudaStreamWaitEvent(s, e_b[j], 0));
-        for (int c = 0; c < chunks && st == SPMM_OK; ++c) {
-            const int rows = r[c + 1] - r[c];
-            const long long p0 = row_ptr[r[c]], cnnz = row_ptr[r[c + 1]] - p0;
-            int* rp_c = reinterpret_cast<int*>(base + off_rp[c]);
-            if (j == 0) {  // chunk c arrives once: rebase its row offsets to start at 0
-                st = cuda_status(cudaStreamWaitEvent(s, e_a[c], 0));
-                if (st == SPMM_OK && p0 != 0) {
-                    rebase_kernel<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(rp_c, rows + 1, (int)p0);
-                    const cudaError_t x = cudaGetLastError();
-                    if (x == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
-                    st = cuda_status(x);
+    for (size_t q = 0; q < P.size() && st == SPMM_OK; ++q) {
+        const Prod& p = P[q];
+        unsigned char* d_B = base + p.off_B;
+        unsigned char* d_C = base + p.off_C;
+        const long long ldc = ldc_of[prods[q]];
+        for (int j = 0; j < p.slabs && st == SPMM_OK; ++j) {
+            const long long c0 = j * p.w, cw = std::min<long long>(p.w, p.n - c0);
+            st = cuda_status(cudaStreamWaitEvent(s, ev[ev_b[q] + j], 0));
+            for (int c = 0; c < chunks && st == SPMM_OK; ++c) {
+                const int rows = r[c + 1] - r[c];
+                const long long p0 = row_ptr[r[c]], cnnz = row_ptr[r[c + 1]] - p0;
+                int* rp_c = reinterpret_cast<int*>(base + off_rp[c]);
+                if (q == 0 && j == 0) {  // chunk c arrives once: rebase its row offsets to start at 0
+                    st = cuda_status(cudaStreamWaitEvent(s, e_a[c], 0));
+                    if (st == SPMM_OK && p0 != 0) {
+                        rebase_kernel<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(rp_c, rows + 1, (int)p0);
+                        const cudaError_t x = cudaGetLastError();
+                        if (x == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+                        st = cuda_status(x);
+                    }
                 }
-            }
-            if (st == SPMM_OK && rows > 0)
-                st = spmm_csr_ex(rows, k, (int)cw, cnnz, rp_c, reinterpret_cast<const int*>(base + off_col[c]),
-                                 base + off_val[c], vals_type, d_B + c0 * sb,
-                                 b_type, ldb_d, d_C + ((size_t)r[c] * ldc_d + c0) * sc, c_type, ldc_d, alg, &t,
-                                 ws_need ? base + off_ws : nullptr, ws_need, nullptr, stream);
-            cudaEvent_t done = e_c[(size_t)j * chunks + c];
-            if (st == SPMM_OK) st = cuda_status(cudaEventRecord(done, s));
-            if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, done, 0));
-            if (st == SPMM_OK && rows > 0) {
-                unsigned char* hc = static_cast<unsigned char*>(C) + ((size_t)r[c] * ldc + c0) * sc;
-                const unsigned char* dc = d_C + ((size_t)r[c] * ldc_d + c0) * sc;
-                st = cuda_status((slabs == 1 && ldc == ldc_d)
-                                     ? cudaMemcpyAsync(hc, dc, (size_t)rows * ldc_d * sc, cudaMemcpyDeviceToHost, down)
-                                     : cudaMemcpy2DAsync(hc, (size_t)ldc * sc, dc, (size_t)ldc_d * sc, (size_t)cw * sc,
-                                                         (size_t)rows, cudaMemcpyDeviceToHost, down));
+                if (st == SPMM_OK && rows > 0)
+                    st = spmm_csr_ex(rows, k, (int)cw, cnnz, rp_c, reinterpret_cast<const int*>(base + off_col[c]),
+                                     base + off_val[c], vals_type, d_B + c0 * sb, b_type, p.ldb_d,
+                                     d_C + ((size_t)r[c] * p.ldc_d + c0) * sc, c_type, p.ldc_d, p.alg, &t,
+                                     ws_need ? base + off_ws : nullptr, ws_need, nullptr, stream);
+                cudaEvent_t done = ev[ev_c[q] + (size_t)j * chunks + c];
+                if (st == SPMM_OK) st = cuda_status(cudaEventRecord(done, s));
+                if (st == SPMM_OK) st = cuda_status(cudaStreamWaitEvent(down, done, 0));
+                if (st == SPMM_OK && rows > 0) {
+                    unsigned char* hc = static_cast<unsigned char*>(C_of[prods[q]]) + ((size_t)r[c] * ldc + c0) * sc;
+                    const unsigned char* dc = d_C + ((size_t)r[c] * p.ldc_d + c0) * sc;
+                    st = cuda_status((p.slabs == 1 && ldc == p.ldc_d)
+                                         ? cudaMemcpyAsync(hc, dc, (size_t)rows * p.ldc_d * sc, cudaMemcpyDeviceToHost,
+                                                           down)
+                                         : cudaMemcpy2DAsync(hc, (size_t)ldc * sc, dc, (size_t)p.ldc_d * sc,
+                                                             (size_t)cw * sc, (size_t)rows, cudaMemcpyDeviceToHost,
+                                                             down));
+                }
             }
         }
     }
@@ -950,15 +996,26 @@ static int host_product(int m, int k, int n, const int* row_ptr, const int* col_
 int spmm_csr_host(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
                   const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
                   const spmm_tuning_t* tuning, void* stream) {
-    return host_product(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
-                        stream, true);
+    if (n < 0) return SPMM_ERR_INVALID_VALUE;
+    void* Cs[1] = {C};
+    return host_products(m, k, row_ptr, col_ind, vals, vals_type, 1, &n, &B, b_type, &ldb, Cs, c_type, &ldc, alg,
+                         tuning, stream, true);
 }
 
 int spmm_csr_host_async(int m, int k, int n, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
                         const void* B, int b_type, long long ldb, void* C, int c_type, long long ldc, int alg,
                         const spmm_tuning_t* tuning, void* stream) {
-    return host_product(m, k, n, row_ptr, col_ind, vals, vals_type, B, b_type, ldb, C, c_type, ldc, alg, tuning,
-                        stream, false);
+    if (n < 0) return SPMM_ERR_INVALID_VALUE;
+    void* Cs[1] = {C};
+    return host_products(m, k, row_ptr, col_ind, vals, vals_type, 1, &n, &B, b_type, &ldb, Cs, c_type, &ldc, alg,
+                         tuning, stream, false);
+}
+
+int spmm_csr_host_multi(int m, int k, const int* row_ptr, const int* col_ind, const void* vals, int vals_type,
+                        int count, const int* n, const void* const* B, int b_type, const long long* ldb, void* const* C,
+                        int c_type, const long long* ldc, int alg, const spmm_tuning_t* tuning, void* stream) {
+    return host_products(m, k, row_ptr, col_ind, vals, vals_type, count, n, B, b_type, ldb, C, c_type, ldc, alg,
+                         tuning, stream, false);
 }
 
 int spmm_debug_bounded_wait(int* d_status, long long limit_ns, void* stream) {

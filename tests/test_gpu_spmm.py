@@ -405,6 +405,58 @@ def test_host_async_back_to_back(gpu_lib):
         assert torch.equal(c0, c1)
 
 
+@pytest.mark.parametrize("alg", ["auto_gb300", "merge", "hybrid", "row_split"])
+def test_host_multi_matches_single_calls(gpu_lib, alg):
+    """spmm_csr_host_multi: several widths (one of them 0, one needing the scalar path, one
+    large enough for column slabs) against one matrix of four row chunks, A uploaded once.
+    Each C_i must equal the oracle and, bit for bit, what spmm_csr_host gives for that width
+    alone (same blocks, same kernels); a second call through the same pool gives the same bits."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(31)
+    lens = rng.integers(0, 40, 180_000)
+    lens[1234] = 150_000
+    a = csr_arrays(lens, 200_000, 32)
+    k = 200_000
+    widths = [8, 0, 13, 64, 128]
+    rp, ci, v = (torch.from_numpy(x).pin_memory() for x in a)
+    Bs = [torch.from_numpy(gen.normal_matrix(k, n, 40 + i)).pin_memory() for i, n in enumerate(widths)]
+    runs = []
+    for _ in range(2):
+        Cs = [torch.full((len(a[0]) - 1, n), float("nan")).pin_memory() for n in widths]
+        pkg.spmm_host_multi(rp, ci, v, Bs, Cs, alg=alg)
+        torch.cuda.current_stream().synchronize()
+        runs.append(Cs)
+    for n, B, C0, C1 in zip(widths, Bs, *runs):
+        if n == 0:
+            continue
+        check(C0.numpy(), *a, B.numpy())
+        single = torch.empty_like(C0).pin_memory()
+        pkg.spmm_host(rp, ci, v, B, single, alg=alg)
+        assert torch.equal(C0, single), n
+        assert torch.equal(C0, C1), n
+
+
+def test_host_multi_16bit_and_empty(gpu_lib):
+    """16-bit storage through the multi-product entry, and a call with no products."""
+    import torch
+
+    pkg = gpu_lib
+    rp, ci, v, k = structure("power_law")
+    vb = torch.from_numpy(v).to(torch.bfloat16).pin_memory()
+    rpt, cit = torch.from_numpy(rp).pin_memory(), torch.from_numpy(ci).pin_memory()
+    Bs = [torch.from_numpy(gen.normal_matrix(k, n, 50 + n)).to(torch.bfloat16).pin_memory() for n in (16, 48)]
+    Cs = [torch.empty((len(rp) - 1, B.shape[1]), dtype=torch.bfloat16).pin_memory() for B in Bs]
+    pkg.spmm_host_multi(rpt, cit, vb, Bs, Cs, alg="auto_gb300")
+    torch.cuda.current_stream().synchronize()
+    for B, C in zip(Bs, Cs):
+        single = torch.empty_like(C).pin_memory()
+        pkg.spmm_host(rpt, cit, vb, B, single, alg="auto_gb300")
+        assert torch.equal(C, single)
+    assert pkg.spmm_host_multi(rpt, cit, vb, [], []) == []
+
+
 def test_host_calls_chained_through_host_memory(gpu_lib):
     """The C of an asynchronous host-buffer call is the B of the next call.  The
     synchronous entry orders its uploads after the work already queued on the

@@ -165,6 +165,50 @@ def test_host_entries_check_arguments_on_the_host(lib):
         assert np.all(C == 0)
 
 
+def test_host_multi_checks_arguments_on_the_host(lib):
+    """spmm_csr_host_multi rejects a bad product (or bad arrays) before any CUDA call, and
+    returns at once when there is nothing to compute."""
+    import ctypes
+
+    import numpy as np
+
+    rp = np.array([0, 1, 2, 3, 4], dtype=np.int32)
+    ci = np.arange(4, dtype=np.int32)
+    v = np.ones(4, dtype=np.float32)
+    Bs = [np.ones((4, 8), dtype=np.float32), np.ones((4, 4), dtype=np.float32)]
+    Cs = [np.zeros((4, 8), dtype=np.float32), np.zeros((4, 4), dtype=np.float32)]
+    F = pkg.F32
+
+    def arrays(ns, ldbs, ldcs):
+        cnt = len(ns)
+        keep = [(ctypes.c_int * cnt)(*ns), (ctypes.c_void_p * cnt)(*[b.ctypes.data for b in Bs[:cnt]]),
+                (ctypes.c_longlong * cnt)(*ldbs), (ctypes.c_void_p * cnt)(*[c.ctypes.data for c in Cs[:cnt]]),
+                (ctypes.c_longlong * cnt)(*ldcs)]
+        return keep, [ctypes.addressof(x) for x in keep]
+
+    def call(ns=(8, 4), ldbs=(8, 4), ldcs=(8, 4), m=4, count=None, alg=pkg.ALG_MERGE, b_type=F, row_ptr=rp.ctypes.data):
+        keep, (n, b, ldb, c, ldc) = arrays(list(ns), list(ldbs), list(ldcs))
+        return pkg.spmm_csr_host_multi(m, 4, row_ptr, ci.ctypes.data, v.ctypes.data, F,
+                                       len(ns) if count is None else count, n, b, b_type, ldb, c, F, ldc, alg, None,
+                                       None)
+
+    assert call(m=-1) == pkg.ERR_INVALID_VALUE
+    assert call(count=-1) == pkg.ERR_INVALID_VALUE
+    assert call(row_ptr=None) == pkg.ERR_INVALID_VALUE
+    assert call(ns=(8, -4)) == pkg.ERR_INVALID_VALUE
+    assert call(ldbs=(8, 3)) == pkg.ERR_INVALID_VALUE  # the second product's ldb < n
+    assert call(ldcs=(4, 4)) == pkg.ERR_INVALID_VALUE
+    assert call(alg=9) == pkg.ERR_INVALID_VALUE
+    assert call(b_type=pkg.F16) == pkg.ERR_UNSUPPORTED
+    assert call(m=0) == pkg.OK
+    assert call(ns=(0, 0)) == pkg.OK
+    assert pkg.spmm_csr_host_multi(4, 4, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, F, 0, None, None, F, None,
+                                   None, F, None, pkg.ALG_MERGE, None, None) == pkg.OK
+    assert pkg.spmm_csr_host_multi(4, 4, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, F, 2, None, None, F, None,
+                                   None, F, None, pkg.ALG_MERGE, None, None) == pkg.ERR_INVALID_VALUE
+    assert all(np.all(C == 0) for C in Cs)
+
+
 def test_semiring_argument_checks(lib):
     good = dict(m=4, k=4, n=4, nnz=4, row_ptr=8, col_ind=16, vals=32, B=64, ldb=4, C=128, ldc=4,
                 semiring=pkg.SEMIRING_MIN_PLUS, alg=0, tuning=None, workspace=None, workspace_bytes=0, d_status=None,
