@@ -26,7 +26,7 @@ def run(pkg, torch, rp, ci, v, B, alg, **kw):
 
 @pytest.mark.parametrize("name", STRUCTURES)
 @pytest.mark.parametrize("alg", ALGS)
-@pytest.mark.parametrize("n", [1, 4, 8, 13, 64, 128, 300])
+@pytest.mark.parametrize("n", [1, 4, 8, 13, 40, 64, 128, 300])
 def test_structures(gpu_lib, name, alg, n):
     import torch
 
