@@ -441,7 +441,9 @@ typedef enum {
                                    run about 2x slower than the row chunks                      */
     SPMM_BATCHED_AUTOTUNE = 1,  /* per matrix: the autotuner's pick for its shape bucket            */
     SPMM_BATCHED_ROW_SPLIT = 2, /* every matrix row split                                            */
-    SPMM_BATCHED_MERGE = 3      /* every matrix merge based                                          */
+    SPMM_BATCHED_MERGE = 3,     /* every matrix merge based                                          */
+    SPMM_BATCHED_ROW_SPLIT_X2 = 4 /* every matrix row split, read with two 16-byte vectors per lane
+                                   where n, ldb and ldc are multiples of 8 (one elsewhere)        */
 } spmm_batched_policy_t;
 
 /*
@@ -451,18 +453,23 @@ typedef enum {
  * one device allocation (work list, merge partitions, carry buffers) and
  * synchronises `stream` once.  SPMM_BATCHED_AUTOTUNE times, for every shape
  * bucket (n, floor(log2 m), mean row length class) not yet in the process-wide
- * cache, row split with the full lane group of the width and with a half and a
- * quarter of it (twice and four times the column slabs), and merge based with
- * three tile sizes, on a sample of the plan's matrices of that bucket (up to
- * 64 matrices or 4M rows + nonzeros), and keeps the fastest.
+ * cache, row split with one and with two 16-byte vectors per lane (the latter
+ * when n, ldb and ldc are multiples of 8), each with the full lane group of
+ * the width and with a half and a quarter of it (twice and four times the
+ * column slabs), and merge based with three tile sizes, on a sample of the
+ * plan's matrices of that bucket (up to 64 matrices or 4M rows + nonzeros,
+ * repeated to 32M rows + nonzeros so that it is timed on a busy GPU), and
+ * keeps the fastest.  The row split of a plan runs as one persistent kernel
+ * per access width that its matrices use.
  */
 int spmm_batched_plan_create(int count, const spmm_batch_matrix_t *mats, int policy, void *stream,
                              spmm_batched_plan_t **plan);
 
-/* Enqueue the batch: a persistent kernel over the row-split chunks (on a
-   stream of the plan's own, forked from and joined back to `stream`, when the
-   plan also has merge tiles), a persistent kernel over the merge tiles and the
-   fix-up (up to three launches, after a memset of the work counters).  Both
+/* Enqueue the batch: a persistent kernel over the row-split chunks of each
+   access width the plan uses (on a stream of the plan's own, forked from and
+   joined back to `stream`, when the plan also has merge tiles), a persistent
+   kernel over the merge tiles and the fix-up (up to four launches, after a
+   memset of the work counters).  Both
    persistent kernels take their work items from a counter, in the plan's
    order: row chunks of the largest matrices first.  Runs of one plan share its
    counters and carry buffers: they must not overlap on the GPU. */

@@ -472,7 +472,7 @@ from .autograd import CSRMatrix, SpMMFunction, spmm_autograd  # noqa: E402,F401
 
 # ----------------------------------------------------------------------------- batched form
 
-BATCHED_MODEL, BATCHED_AUTOTUNE, BATCHED_ROW_SPLIT, BATCHED_MERGE = 0, 1, 2, 3
+BATCHED_MODEL, BATCHED_AUTOTUNE, BATCHED_ROW_SPLIT, BATCHED_MERGE, BATCHED_ROW_SPLIT_X2 = 0, 1, 2, 3, 4
 
 
 class SpmmBatchMatrix(ctypes.Structure):

@@ -25,7 +25,7 @@ namespace spmm {
 namespace {
 
 struct MatDesc {
-    int m, k, n, alg, W, slabs, ips, num_tiles, tile_base;
+    int m, k, n, alg, W, vec, slabs, ips, num_tiles, tile_base;  // vec: B / C columns per lane access (4 or 8)
     long long nnz, ldb, ldc;
     const int* row_ptr;
     const int* col_ind;
@@ -45,14 +45,26 @@ struct Item {
 
 constexpr int kRowsPerGroupPerItem = 8;
 
-template <int W>
+template <int W, int VEC>
 __device__ __forceinline__ void batched_rows(const MatDesc& d, int r0, int r1, int slab) {
     RowSplitArgs ra{d.m, d.n, d.row_ptr, d.col_ind, d.vals, d.B, d.ldb, d.C, d.ldc};
     constexpr int G = kThreads / W;
     const int g = threadIdx.x / W;
     for (int base = r0; base < r1; base += G) {  // same trip count for the whole CTA
         const int row = base + g;
-        rowsplit_row<float, float, float, 4, W>(ra, row < r1 ? row : d.m, slab);
+        rowsplit_row<float, float, float, VEC, W>(ra, row < r1 ? row : d.m, slab);
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void batched_rows_any(const MatDesc& d, int r0, int r1, int slab) {
+    switch (d.W) {
+        case 1: batched_rows<1, VEC>(d, r0, r1, slab); break;
+        case 2: batched_rows<2, VEC>(d, r0, r1, slab); break;
+        case 4: batched_rows<4, VEC>(d, r0, r1, slab); break;
+        case 8: batched_rows<8, VEC>(d, r0, r1, slab); break;
+        case 16: batched_rows<16, VEC>(d, r0, r1, slab); break;
+        default: batched_rows<32, VEC>(d, r0, r1, slab); break;
     }
 }
 
@@ -102,22 +114,17 @@ __device__ __forceinline__ long long next_item(unsigned long long* counter) {
 }
 
 // Row-split items: a lean kernel of its own (no shared memory, the row
-// split's registers), so that it runs at the occupancy of the row split.
+// split's registers), so that it runs at the occupancy of the row split; one
+// instantiation per access width VEC (the plan keeps the matrices of each
+// width in a range of items of its own).
+template <int VEC>
 __global__ void __launch_bounds__(kThreads)
     batched_rows_kernel(const MatDesc* __restrict__ mats, const Item* __restrict__ items, long long n_items,
                         unsigned long long* counter) {
     for (long long it = next_item(counter); it < n_items; it = next_item(counter)) {
         const Item item = items[it];
         const MatDesc d = mats[item.mat];
-        const int slab = item.kind_slab >> 1;
-        switch (d.W) {
-            case 1: batched_rows<1>(d, item.a, item.b, slab); break;
-            case 2: batched_rows<2>(d, item.a, item.b, slab); break;
-            case 4: batched_rows<4>(d, item.a, item.b, slab); break;
-            case 8: batched_rows<8>(d, item.a, item.b, slab); break;
-            case 16: batched_rows<16>(d, item.a, item.b, slab); break;
-            default: batched_rows<32>(d, item.a, item.b, slab); break;
-        }
+        batched_rows_any<VEC>(d, item.a, item.b, item.kind_slab >> 1);
     }
 }
 
@@ -215,10 +222,21 @@ size_t merge_smem_bytes(int W, int ips) {
 struct Choice {
     int alg;
     int ips_scale;  // merge: ips = default * 2^ips_scale (ips_scale in {-1, 0, 1})
-    int lanes_div;  // row split: lanes per row = lanes_for(n) / lanes_div (1, 2 or 4; more column slabs)
+    int lanes_div;  // row split: lanes per row = the full lane group / lanes_div (1, 2 or 4; more column slabs)
+    int vec;        // row split: columns per lane access, 4 (one 16-byte vector) or 8 (two)
 };
 
-int lanes_of(int n, int lanes_div) { return std::max(1, lanes_for(std::max(n, 1)) / std::max(1, lanes_div)); }
+// Lanes per row of the row split for width n and vec columns per lane: the power of two covering
+// the row's vectors (at most 32), divided by lanes_div.
+int lanes_of(int n, int lanes_div, int vec = 4) {
+    const int chunks = (std::max(n, 1) + vec - 1) / vec;
+    int W = 1;
+    while (W < chunks && W < 32) W <<= 1;
+    return std::max(1, W / std::max(1, lanes_div));
+}
+
+// Two 16-byte vectors per lane need n, ldb and ldc to be multiples of 8.
+bool two_vectors_ok(const spmm_batch_matrix_t& mt) { return mt.n % 8 == 0 && mt.ldb % 8 == 0 && mt.ldc % 8 == 0; }
 
 using BucketKey = std::tuple<int, int, int, int>;  // (device SMs, n, floor(log2 m), mean-row-length bucket)
 std::mutex g_tune_mu;
@@ -242,18 +260,21 @@ struct spmm_batched_plan {
     std::vector<int> algs;
     std::vector<int> ips;
     std::vector<int> lanes;  // lanes per row of each matrix
+    std::vector<int> vecs;   // columns per lane access of each matrix
     unsigned char* mem = nullptr;
     MatDesc* d_mats = nullptr;
     Item* d_items = nullptr;       // row-split items, then merge-tile items
     long long n_items = 0;
-    long long n_row_items = 0;
+    long long n_row_items = 0;   // row-split items (one-vector matrices first, then two-vector ones)
+    long long n_row_items8 = 0;  // of which the last ones, of matrices read with two vectors per lane
+    int grid_rows8 = 0;
     int grid_rows = 0;
     int total_tiles = 0;
     int* d_tile_mat = nullptr;
     int* d_carry_row = nullptr;
     int* d_head_row = nullptr;
     int* d_status = nullptr;
-    unsigned long long* d_counters = nullptr;  // work-item counters of the two persistent kernels
+    unsigned long long* d_counters = nullptr;  // work-item counters of the persistent kernels (tiles, rows, rows x2)
     cudaStream_t side = nullptr;                // the row-split kernel runs here, beside the merge tiles
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t smem = 0;
@@ -278,12 +299,13 @@ void destroy_plan(spmm_batched_plan* p) {
 
 // Build a plan for matrices `mats` with per-matrix (alg, ips) already chosen.
 int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<int>& algs, const std::vector<int>& ips,
-               const std::vector<int>& lanes, cudaStream_t s, spmm_batched_plan** out) {
+               const std::vector<int>& lanes, const std::vector<int>& vecs, cudaStream_t s, spmm_batched_plan** out) {
     auto* p = new spmm_batched_plan();
     p->count = (int)mats.size();
     p->algs = algs;
     p->ips = ips;
     p->lanes = lanes;
+    p->vecs = vecs;
     p->mats = mats;
     cudaGetDevice(&p->device);
     std::vector<MatDesc> descs(mats.size());
@@ -308,7 +330,8 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
         d.C = mt.C;
         d.alg = algs[b];
         d.W = lanes[b];
-        d.slabs = ((mt.n + 3) / 4 + d.W - 1) / d.W;
+        d.vec = d.alg == SPMM_ALG_MERGE ? 4 : vecs[b];
+        d.slabs = ((mt.n + d.vec - 1) / d.vec + d.W - 1) / d.W;
         d.ips = ips[b];
         d.tile_base = (int)tile_mat.size();
         if (mt.m == 0 || mt.n == 0) {
@@ -331,8 +354,13 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     }
     // row-split chunks, largest matrices first: the big matrices' rows of B are then gathered
     // while few other matrices compete for L2, and the small ones fill the tail of the launch
-    std::stable_sort(row_mats.begin(), row_mats.end(), [&](int x, int y) { return mats[x].nnz > mats[y].nnz; });
+    std::stable_sort(row_mats.begin(), row_mats.end(), [&](int x, int y) {
+        if (descs[x].vec != descs[y].vec) return descs[x].vec < descs[y].vec;  // one-vector matrices first
+        return mats[x].nnz > mats[y].nnz;
+    });
+    long long first8 = -1;
     for (const int b : row_mats) {
+        if (descs[b].vec == 8 && first8 < 0) first8 = (long long)items.size();
         const auto& mt = mats[b];
         const MatDesc& d = descs[b];
         const int chunk = kRowsPerGroupPerItem * (kThreads / d.W);
@@ -340,6 +368,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
             for (int r = 0; r < mt.m; r += chunk) items.push_back(Item{b, sl << 1, r, std::min(mt.m, r + chunk)});
     }
     p->n_row_items = (long long)items.size();
+    p->n_row_items8 = first8 < 0 ? 0 : p->n_row_items - first8;
     items.insert(items.end(), tile_items.begin(), tile_items.end());
     p->n_items = (long long)items.size();
     p->total_tiles = (int)tile_mat.size();
@@ -396,11 +425,13 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     p->smem = smem;
     if (st == SPMM_OK && smem > 48 * 1024)
         st = status_of(cudaFuncSetAttribute(batched_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int blocks = 0, blocks_rows = 0, sms = 0;
+    int blocks = 0, blocks_rows = 0, blocks_rows8 = 0, sms = 0;
     if (st == SPMM_OK)
         st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batched_tiles_kernel, kThreads, smem));
     if (st == SPMM_OK)
-        st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_rows, batched_rows_kernel, kThreads, 0));
+        st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_rows, batched_rows_kernel<4>, kThreads, 0));
+    if (st == SPMM_OK)
+        st = status_of(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_rows8, batched_rows_kernel<8>, kThreads, 0));
     if (st == SPMM_OK) st = status_of(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     if (st == SPMM_OK && p->n_row_items > 0 && p->n_items > p->n_row_items) {
         st = status_of(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
@@ -413,8 +444,10 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
     }
     const long long n_tile_items = p->n_items - p->n_row_items;
     p->grid = (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks, 1) * sms, n_tile_items));
-    p->grid_rows =
-        (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks_rows, 1) * sms, p->n_row_items));
+    const long long n_row4 = p->n_row_items - p->n_row_items8;
+    p->grid_rows = (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks_rows, 1) * sms, n_row4));
+    p->grid_rows8 =
+        (int)std::max<long long>(1, std::min<long long>((long long)std::max(blocks_rows8, 1) * sms, p->n_row_items8));
     *out = p;
     return SPMM_OK;
 }
@@ -425,7 +458,7 @@ int build_plan(const std::vector<spmm_batch_matrix_t>& mats, const std::vector<i
 int run_plan(const spmm_batched_plan* p, cudaStream_t s) {
     const long long n_tile_items = p->n_items - p->n_row_items;
     if (p->n_items > 0) {
-        const cudaError_t e = cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), s);
+        const cudaError_t e = cudaMemsetAsync(p->d_counters, 0, 3 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return status_of(e);
     }
     const bool fork = p->side && n_tile_items > 0 && p->n_row_items > 0;
@@ -437,9 +470,15 @@ int run_plan(const spmm_batched_plan* p, cudaStream_t s) {
         rs = p->side;
     }
     int st = SPMM_OK;
-    if (p->n_row_items > 0) {
-        batched_rows_kernel<<<p->grid_rows, kThreads, 0, rs>>>(p->d_mats, p->d_items, p->n_row_items,
-                                                               p->d_counters + 1);
+    const long long n_row4 = p->n_row_items - p->n_row_items8;
+    if (n_row4 > 0) {
+        batched_rows_kernel<4><<<p->grid_rows, kThreads, 0, rs>>>(p->d_mats, p->d_items, n_row4, p->d_counters + 1);
+        st = status_of(cudaGetLastError());
+        if (st == SPMM_OK) g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (st == SPMM_OK && p->n_row_items8 > 0) {
+        batched_rows_kernel<8><<<p->grid_rows8, kThreads, 0, rs>>>(p->d_mats, p->d_items + n_row4, p->n_row_items8,
+                                                                   p->d_counters + 2);
         st = status_of(cudaGetLastError());
         if (st == SPMM_OK) g_launches.fetch_add(1, std::memory_order_relaxed);
     }
@@ -466,14 +505,15 @@ int run_plan(const spmm_batched_plan* p, cudaStream_t s) {
 
 // Time one candidate schedule for a sample of matrices (median of 3 runs, ms).
 float time_candidate(const std::vector<spmm_batch_matrix_t>& sample, const Choice& c, cudaStream_t s) {
-    std::vector<int> algs(sample.size(), c.alg), ips(sample.size()), lanes(sample.size());
+    std::vector<int> algs(sample.size(), c.alg), ips(sample.size()), lanes(sample.size()), vecs(sample.size(), 4);
     for (size_t i = 0; i < sample.size(); ++i) {
-        lanes[i] = c.alg == SPMM_ALG_MERGE ? lanes_for(std::max(sample[i].n, 1)) : lanes_of(sample[i].n, c.lanes_div);
+        if (c.alg != SPMM_ALG_MERGE && c.vec == 8 && two_vectors_ok(sample[i])) vecs[i] = 8;
+        lanes[i] = c.alg == SPMM_ALG_MERGE ? lanes_for(std::max(sample[i].n, 1)) : lanes_of(sample[i].n, c.lanes_div, vecs[i]);
         const int d = default_ips(lanes[i]);
         ips[i] = c.ips_scale > 0 ? d * 2 : c.ips_scale < 0 ? std::max(4, d / 2) : d;
     }
     spmm_batched_plan* p = nullptr;
-    if (build_plan(sample, algs, ips, lanes, s, &p) != SPMM_OK) return INFINITY;
+    if (build_plan(sample, algs, ips, lanes, vecs, s, &p) != SPMM_OK) return INFINITY;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -504,7 +544,7 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
                              spmm_batched_plan_t** plan) {
     if (!plan || count < 0 || (count > 0 && !mats)) return SPMM_ERR_INVALID_VALUE;
     if (policy != SPMM_BATCHED_MODEL && policy != SPMM_BATCHED_AUTOTUNE && policy != SPMM_BATCHED_ROW_SPLIT &&
-        policy != SPMM_BATCHED_MERGE)
+        policy != SPMM_BATCHED_MERGE && policy != SPMM_BATCHED_ROW_SPLIT_X2)
         return SPMM_ERR_INVALID_VALUE;
     *plan = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
@@ -567,16 +607,21 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
                 }
                 work += w;
             }
-            // candidates: row split with the full lane group and with 1/2 and 1/4 of it (column
-            // slabs), merge based with three tile sizes
-            std::vector<Choice> cands = {{SPMM_ALG_ROW_SPLIT, 0, 1}, {SPMM_ALG_ROW_SPLIT, 0, 2},
-                                         {SPMM_ALG_ROW_SPLIT, 0, 4}, {SPMM_ALG_MERGE, 0, 1},
-                                         {SPMM_ALG_MERGE, -1, 1}, {SPMM_ALG_MERGE, 1, 1}};
+            // candidates: row split with one and with two 16-byte vectors per lane, each with the
+            // full lane group and with 1/2 and 1/4 of it (column slabs); merge based with three
+            // tile sizes
+            std::vector<Choice> cands = {{SPMM_ALG_ROW_SPLIT, 0, 1, 4}, {SPMM_ALG_ROW_SPLIT, 0, 2, 4},
+                                         {SPMM_ALG_ROW_SPLIT, 0, 4, 4}, {SPMM_ALG_ROW_SPLIT, 0, 1, 8},
+                                         {SPMM_ALG_ROW_SPLIT, 0, 2, 8}, {SPMM_ALG_ROW_SPLIT, 0, 4, 8},
+                                         {SPMM_ALG_MERGE, 0, 1, 4},     {SPMM_ALG_MERGE, -1, 1, 4},
+                                         {SPMM_ALG_MERGE, 1, 1, 4}};
             Choice best = cands[0];
             float best_ms = INFINITY;
             const int n0 = v[kv.second[0]].n;  // every matrix of a bucket has the same n
+            const bool two_ok = two_vectors_ok(v[kv.second[0]]);
             for (const Choice& c : cands) {
-                if (c.lanes_div > 1 && lanes_of(n0, c.lanes_div) == lanes_of(n0, c.lanes_div / 2))
+                if (c.vec == 8 && !two_ok) continue;
+                if (c.lanes_div > 1 && lanes_of(n0, c.lanes_div, c.vec) == lanes_of(n0, c.lanes_div / 2, c.vec))
                     continue;  // no narrower lane group for this width
                 const float ms = time_candidate(sample, c, s);
                 if (ms < best_ms) {
@@ -588,11 +633,13 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
             g_tune_cache[kv.first] = best;
         }
     }
-    std::vector<int> lanes(v.size());
+    std::vector<int> lanes(v.size()), vecs(v.size(), 4);
     for (size_t b = 0; b < v.size(); ++b) {
-        int alg = SPMM_ALG_ROW_SPLIT, sc = 0, div = 1;
+        int alg = SPMM_ALG_ROW_SPLIT, sc = 0, div = 1, vec = 4;
         if (policy == SPMM_BATCHED_MERGE) {
             alg = SPMM_ALG_MERGE;
+        } else if (policy == SPMM_BATCHED_ROW_SPLIT_X2) {
+            vec = two_vectors_ok(v[b]) ? 8 : 4;
         } else if (policy == SPMM_BATCHED_MODEL) {
             // Inside the batch the merge tiles run about 2x slower than the row chunks (no bulk-copy
             // staging, 24 warps per SM; measured on the 2048-matrix batch: every matrix merge 23.9 ms,
@@ -600,20 +647,24 @@ int spmm_batched_plan_create(int count, const spmm_batch_matrix_t* mats, int pol
             // matrix's row chunks the critical path (the Type 1 guard of the GB300 selector)
             const bool type1 = lmax[b] > 1024 && lmax[b] * 8192 > v[b].nnz;
             alg = type1 ? SPMM_ALG_MERGE : SPMM_ALG_ROW_SPLIT;
+            // one 16-byte vector per lane: two made the 2048-matrix batch slower (10.1 -> 12.8 ms)
         } else if (policy == SPMM_BATCHED_AUTOTUNE) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             const Choice c = g_tune_cache[bucket_of(sms, v[b])];
             alg = c.alg;
             sc = c.ips_scale;
             div = c.lanes_div;
+            vec = c.vec == 8 && two_vectors_ok(v[b]) ? 8 : 4;
         }
-        lanes[b] = alg == SPMM_ALG_MERGE ? lanes_for(std::max(v[b].n, 1)) : lanes_of(v[b].n, div);
+        if (alg == SPMM_ALG_MERGE) vec = 4;
+        vecs[b] = vec;
+        lanes[b] = alg == SPMM_ALG_MERGE ? lanes_for(std::max(v[b].n, 1)) : lanes_of(v[b].n, div, vec);
         const int d = default_ips(lanes[b]);
         algs[b] = alg;
         ips[b] = sc > 0 ? d * 2 : sc < 0 ? std::max(4, d / 2) : d;
     }
     spmm_batched_plan* p = nullptr;
-    const int st = build_plan(v, algs, ips, lanes, s, &p);
+    const int st = build_plan(v, algs, ips, lanes, vecs, s, &p);
     if (st != SPMM_OK) return st;
     p->max_row = lmax;
     *plan = p;
@@ -660,7 +711,8 @@ int spmm_batched_launch_graph(const spmm_batched_plan_t* plan, void* stream) {
     if (!plan || !plan->exec) return SPMM_ERR_INVALID_VALUE;
     const cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
     if (e == cudaSuccess)
-        g_launches.fetch_add((plan->n_row_items > 0) + (plan->n_items > plan->n_row_items) + (plan->total_tiles > 1),
+        g_launches.fetch_add((plan->n_row_items > plan->n_row_items8) + (plan->n_row_items8 > 0) +
+                                 (plan->n_items > plan->n_row_items) + (plan->total_tiles > 1),
                              std::memory_order_relaxed);
     return status_of(e);
 }
@@ -671,7 +723,7 @@ int spmm_batched_run_unfused(const spmm_batched_plan_t* plan, void* stream) {
         const auto& mt = plan->mats[b];
         spmm_tuning_t t{};
         t.items_per_subwarp = plan->ips[b];
-        t.lanes_per_row = plan->lanes[b];
+        t.lanes_per_row = std::min(32, plan->lanes[b] * plan->vecs[b] / 4);  // the same columns per lane group
         const int st = spmm_csr_ex(mt.m, mt.k, mt.n, mt.nnz, mt.row_ptr, mt.col_ind, mt.vals, SPMM_F32, mt.B, SPMM_F32,
                                    mt.ldb, mt.C, SPMM_F32, mt.ldc, plan->algs[b], &t, nullptr, 0, nullptr, stream);
         if (st != SPMM_OK) return st;

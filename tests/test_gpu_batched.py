@@ -35,27 +35,28 @@ def check_all(host, dev):
         assert err <= FP32_TOL, err
 
 
-@pytest.mark.parametrize("policy", ["model", "autotune", "row_split", "merge"])
+@pytest.mark.parametrize("policy", ["model", "autotune", "row_split", "merge", "row_split_x2"])
 def test_batched_policies(gpu_lib, policy):
     import torch
 
     pkg = gpu_lib
     host, dev = make_batch(torch, 40, 5)
     pol = {"model": pkg.BATCHED_MODEL, "autotune": pkg.BATCHED_AUTOTUNE, "row_split": pkg.BATCHED_ROW_SPLIT,
-           "merge": pkg.BATCHED_MERGE}[policy]
+           "merge": pkg.BATCHED_MERGE, "row_split_x2": pkg.BATCHED_ROW_SPLIT_X2}[policy]
     plan = pkg.BatchedPlan(*[[d[i] for d in dev] for i in range(5)], policy=pol)
     algs, items, tiles = plan.query()
     assert len(algs) == 40 and items > 0
     if policy == "merge":
         assert set(algs) == {pkg.ALG_MERGE} and tiles > 0
-    if policy == "row_split":
+    if policy in ("row_split", "row_split_x2"):
         assert set(algs) == {pkg.ALG_ROW_SPLIT} and tiles == 0
     if policy == "model":
         assert algs[1] == pkg.ALG_MERGE  # heavy row: Type 1 guard
     c0 = pkg.spmm_launch_count()
     plan.run()
     torch.cuda.synchronize()
-    assert pkg.spmm_launch_count() - c0 <= 3  # merge tiles, row chunks, fix-up: independent of the batch size
+    # row chunks (one kernel per access width used), merge tiles, fix-up: independent of the batch size
+    assert pkg.spmm_launch_count() - c0 <= 4
     check_all(host, dev)
     # graph replay, with new values of B between replays
     plan.capture_graph()
@@ -88,13 +89,49 @@ def test_batched_exact_integers(gpu_lib):
         B[:] = rng.integers(-4, 5, B.shape)
         d[2].copy_(torch.from_numpy(a.vals))
         d[3].copy_(torch.from_numpy(B))
-    for pol in (pkg.BATCHED_MERGE, pkg.BATCHED_ROW_SPLIT):
+    for pol in (pkg.BATCHED_MERGE, pkg.BATCHED_ROW_SPLIT, pkg.BATCHED_ROW_SPLIT_X2):
         plan = pkg.BatchedPlan(*[[d[i] for d in dev] for i in range(5)], policy=pol)
         plan.run()
         torch.cuda.synchronize()
         for (a, B), d in zip(host, dev):
             assert np.array_equal(d[4].cpu().numpy(), oracle.spmm(a.row_ptr, a.col_ind, a.vals, B).astype(np.float32))
         plan.close()
+
+
+def test_batched_one_and_two_vector_widths_in_one_plan(gpu_lib):
+    """Under SPMM_BATCHED_ROW_SPLIT_X2 the widths that are multiples of 8 read two 16-byte vectors
+    per lane and the others one: the plan runs one row kernel per width (two launches), and every
+    product must equal the oracle bit for bit on integer data."""
+    import torch
+
+    pkg = gpu_lib
+    rng = np.random.default_rng(17)
+    widths = [36, 32, 44, 64, 200, 12, 128, 8]
+    host, dev = [], []
+    for i, n in enumerate(widths):
+        m = int(rng.integers(50, 3000))
+        lens = rng.integers(0, 40, m)
+        a = gen.csr_from_lengths(lens, m, 200 + i)
+        a.vals[:] = rng.integers(-2, 3, a.nnz)
+        B = rng.integers(-4, 5, size=(m, n)).astype(np.float32)
+        host.append((a, B))
+        dev.append(tuple(torch.from_numpy(x).cuda() for x in (a.row_ptr, a.col_ind, a.vals, B)) +
+                   (torch.full((m, n), float("nan"), device="cuda"),))
+    plan = pkg.BatchedPlan(*[[d[i] for d in dev] for i in range(5)], policy=pkg.BATCHED_ROW_SPLIT_X2)
+    c0 = pkg.spmm_launch_count()
+    plan.run()
+    torch.cuda.synchronize()
+    assert pkg.spmm_launch_count() - c0 == 2  # the one-vector and the two-vector row kernels
+    for (a, B), d in zip(host, dev):
+        assert np.array_equal(d[4].cpu().numpy(), oracle.spmm(a.row_ptr, a.col_ind, a.vals, B).astype(np.float32))
+    plan.capture_graph()
+    for d in dev:
+        d[4].fill_(float("nan"))
+    plan.launch_graph()
+    torch.cuda.synchronize()
+    for (a, B), d in zip(host, dev):
+        assert np.array_equal(d[4].cpu().numpy(), oracle.spmm(a.row_ptr, a.col_ind, a.vals, B).astype(np.float32))
+    plan.close()
 
 
 @pytest.mark.slow
