@@ -13,7 +13,10 @@ namespace spmm {
 
 // Queues of the hybrid row split (rowsplit_block_kernel, rowsplit_segment_kernel).
 // A row of more than long_len nonzeros leaves the row-block pass.  A row of at
-// most mid_len is queued in mid[] and later taken by one lane group.  A longer
+// most mid_len is queued in mid[] and later taken by one lane group: rows of at
+// most mid_split nonzeros from the front of mid[], longer ones from its back, so
+// that the segment pass can take the longer ones first and put rows of similar
+// length in one warp's work item.  A longer
 // row is cut into nseg = min(ceil(len / seg_len), kMaxRowSegs) segments of
 // equal length, each taken by a whole warp: a row of one segment is queued in
 // single[]; a row of several reserves nseg consecutive partial slots, and slot
@@ -29,14 +32,16 @@ __host__ __device__ __forceinline__ int long_row_segments(long long len, int seg
 struct LongRowArgs {
     int long_len;     // rows with more nonzeros than this leave the row-block pass
     int mid_len;      // queued rows of at most this many nonzeros are taken by one lane group
+    int mid_split;    // mid rows of at most this many nonzeros fill mid[] from the front, longer from the back
     int seg_len;      // nonzeros per warp segment of a longer row (before the kMaxRowSegs cap)
     int block_rows;   // rows per warp in the row-block pass (1 .. kMaxBlockRows)
     int max_mid;      // capacity of mid[]
     int max_singles;  // capacity of single[]
     int max_parts;    // capacity of multi[], arrive[] and the rows of partial[]
-    int* counts;      // [4]: single rows queued, partial slots reserved, segment-pass work items taken,
-                      // mid rows queued (zeroed before the row-block pass)
-    int* mid;         // [max_mid]: rows of long_len < len <= mid_len
+    int* counts;      // [5]: single rows queued, partial slots reserved, segment-pass work items taken,
+                      // mid rows queued at the front, at the back (zeroed before the row-block pass)
+    int* mid;         // [max_mid]: rows of long_len < len <= mid_split from index 0 up, rows of
+                      // mid_split < len <= mid_len from index max_mid - 1 down
     int* single;      // [max_singles]: rows of one warp segment
     int2* multi;      // [max_parts]: (row, first partial slot of the row) of the segment in this slot
     int* arrive;      // [max_parts]: segments of a row finished so far, at the row's first partial slot
@@ -102,13 +107,14 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
     // each lane takes a run of the block's rows: weights (length of a short row, else 0) and queue counts
     const int rpl = (nr + 31) / 32;
     const int i0 = min(lane * rpl, nr), i1 = min(i0 + rpl, nr);
-    int wsum = 0, nmid = 0, nsingle = 0, nparts = 0;
+    int wsum = 0, nmid = 0, nmid2 = 0, nsingle = 0, nparts = 0;
     for (int i = i0; i < i1; ++i) {
         const int len = s_rp[i + 1] - s_rp[i];
         if (len <= l.long_len) {
             wsum += len;
         } else if (len <= l.mid_len) {
-            ++nmid;
+            if (len <= l.mid_split) ++nmid;
+            else ++nmid2;
         } else {
             const int ns = long_row_segments(len, l.seg_len);
             if (ns == 1) ++nsingle;
@@ -131,26 +137,30 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
         if (lane == 31) s_w[nr] = incl;
     }
     // queue the longer rows (the slab-0 CTA only): one reservation per queue per warp
-    if (blockIdx.y == 0 && __any_sync(kFullMask, nmid + nsingle + nparts > 0)) {
-        int xm = nmid, xs = nsingle, xp = nparts;  // inclusive prefixes over the lanes
+    if (blockIdx.y == 0 && __any_sync(kFullMask, nmid + nmid2 + nsingle + nparts > 0)) {
+        int xm = nmid, xm2 = nmid2, xs = nsingle, xp = nparts;  // inclusive prefixes over the lanes
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int ym = __shfl_up_sync(kFullMask, xm, off);
+            const int ym2 = __shfl_up_sync(kFullMask, xm2, off);
             const int ys = __shfl_up_sync(kFullMask, xs, off);
             const int yp = __shfl_up_sync(kFullMask, xp, off);
             if (lane >= off) {
                 xm += ym;
+                xm2 += ym2;
                 xs += ys;
                 xp += yp;
             }
         }
-        int bm = 0, bs = 0, bp = 0;
+        int bm = 0, bm2 = 0, bs = 0, bp = 0;
         if (lane == 31) {
             if (xm) bm = atomicAdd(l.counts + 3, xm);
+            if (xm2) bm2 = atomicAdd(l.counts + 4, xm2);
             if (xs) bs = atomicAdd(l.counts + 0, xs);
             if (xp) bp = atomicAdd(l.counts + 1, xp);
         }
         bm = __shfl_sync(kFullMask, bm, 31) + xm - nmid;
+        bm2 = __shfl_sync(kFullMask, bm2, 31) + xm2 - nmid2;
         bs = __shfl_sync(kFullMask, bs, 31) + xs - nsingle;
         bp = __shfl_sync(kFullMask, bp, 31) + xp - nparts;
         for (int i = i0; i < i1; ++i) {
@@ -158,9 +168,11 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
             if (len <= l.long_len) continue;
             const int row = (int)(r0 + i);
             if (len <= l.mid_len) {
-                if (bm < l.max_mid) l.mid[bm] = row;
+                // the front and the back of mid[] together hold at most max_mid rows for a valid matrix;
+                // the segment pass checks that they did not meet
+                const int slot = len <= l.mid_split ? bm++ : l.max_mid - 1 - bm2++;
+                if (slot >= 0 && slot < l.max_mid) l.mid[slot] = row;
                 else report(l.status, SPMM_ERR_BAD_CSR);  // more nonzeros than the workspace was sized for
-                ++bm;
                 continue;
             }
             const int ns = long_row_segments(len, l.seg_len);
@@ -331,11 +343,17 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
     TC* __restrict__ C = static_cast<TC*>(a.C);
     constexpr int NG = 32 / W;               // lane groups per warp
     // segments of rows with several first (the longest rows start earliest), then the single rows, then
-    // the mid rows, NG to a work item
+    // the mid rows, NG to a work item: the longer ones (from the back of mid[]) before the shorter ones
     const int n_multi = min(__ldcg(l.counts + 1), l.max_parts);
     const int n_single = min(__ldcg(l.counts), l.max_singles);
-    const int n_mid = min(__ldcg(l.counts + 3), l.max_mid);
-    const int count = n_multi + n_single + (n_mid + NG - 1) / NG;
+    int n_mid = min(__ldcg(l.counts + 3), l.max_mid);
+    int n_mid2 = min(__ldcg(l.counts + 4), l.max_mid);
+    if (n_mid + n_mid2 > l.max_mid) {  // the two ends met: not a valid matrix for this workspace
+        if (threadIdx.x == 0 && blockIdx.x == 0) report(l.status, SPMM_ERR_BAD_CSR);
+        n_mid2 = l.max_mid - n_mid;
+    }
+    const int items2 = (n_mid2 + NG - 1) / NG;  // work items of the longer mid rows
+    const int count = n_multi + n_single + items2 + (n_mid + NG - 1) / NG;
     const long long items = (long long)count * slabs;
     for (;;) {
         long long item = 0;
@@ -345,8 +363,15 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
         const int slab = (int)(item / count);
         const int i = (int)(item - (long long)slab * count);
         if (i >= n_multi + n_single) {  // one lane group per mid row
-            const int q = (i - n_multi - n_single) * NG + grp;
-            const int r = q < n_mid ? __ldcg(l.mid + q) : -1;
+            const int t = i - n_multi - n_single;
+            int r = -1;
+            if (t < items2) {
+                const int q = t * NG + grp;
+                if (q < n_mid2) r = __ldcg(l.mid + (l.max_mid - 1 - q));
+            } else {
+                const int q = (t - items2) * NG + grp;
+                if (q < n_mid) r = __ldcg(l.mid + q);
+            }
             rowsplit_row<TV, TB, TC, VEC, W, SR>(a, (r < 0 || r >= a.m) ? (long long)a.m : (long long)r, slab);
             continue;
         }

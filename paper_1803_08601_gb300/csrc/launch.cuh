@@ -109,13 +109,13 @@ cudaError_t hybrid_launch_one(const RowSplitArgs& a, const LongRowArgs& l, const
         cached_dev = dev;
         cached_blocks = nb < 1 ? 1 : nb;
     }
-    e = cudaMemsetAsync(l.counts, 0, 4 * sizeof(int), st);
+    e = cudaMemsetAsync(l.counts, 0, 5 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     rowsplit_block_kernel<TV, TB, TC, VEC, W, SR><<<dim3((unsigned)gx, (unsigned)s.slabs), kThreads, 0, st>>>(a, l);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    const long long max_items = (long long)l.max_singles + l.max_parts + (l.max_mid + 32 / W - 1) / (32 / W);
+    const long long max_items = (long long)l.max_singles + l.max_parts + (l.max_mid + 32 / W - 1) / (32 / W) + 1;
     long long sx = (long long)cached_blocks * std::max(sms, 1);
     sx = std::min<long long>(sx, (max_items * s.slabs + warps_per_cta - 1) / warps_per_cta);
     if (sx < 1) sx = 1;

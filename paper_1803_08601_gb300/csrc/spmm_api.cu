@@ -231,12 +231,17 @@ MergeLayout merge_layout(int m, long long nnz, int n, const Shape& s) {
 // takes BS = max(W, kUnroll) nonzeros per batch.  Rows of at most long_len
 // nonzeros stay in the row-block pass (long_len = max(32, BS) unless the
 // caller sets it), whose warps own 128 consecutive rows (64 for W >= 16);
-// queued rows of at most mid_len = 4 long_len go to one lane group each; a
-// warp segment holds 16 warp batches (32 / W lane groups x BS nonzeros each).
+// queued rows of at most mid_len = 4 long_len go to one lane group each; with
+// W >= 4 those of more than mid_split = 2 long_len are taken first, so a warp's
+// work item holds rows of similar length and the longest items do not come
+// last (measured on the 1M x 1M power-law matrix, same box, alternating runs:
+// n = 16 0.199 -> 0.193 ms, n = 32 0.303 -> 0.298 ms; with W = 2, n = 8, it
+// lost 3 %, so there every mid row is one queue); a warp segment holds 16 warp
+// batches (32 / W lane groups x BS nonzeros each).
 // The defaults are the fastest of a sweep of long_len in {16, ..., 256} and
 // block_rows in {64, 128, 256} on a 1M x 1M power-law matrix, n = 8 to 128.
 struct HybridLayout {
-    int long_len, mid_len, seg_len, block_rows, max_mid, max_singles, max_parts;
+    int long_len, mid_len, mid_split, seg_len, block_rows, max_mid, max_singles, max_parts;
     size_t off_counts, off_mid, off_single, off_multi, off_arrive, off_partial, total;
 };
 
@@ -247,6 +252,7 @@ HybridLayout hybrid_layout(int m, long long nnz, int n, const Shape& s, const sp
     const long long long_len = t.long_row_len > 0 ? t.long_row_len : def_long;
     H.long_len = (int)std::min<long long>(long_len, 0x3fffffffLL);
     H.mid_len = (int)std::min<long long>(4 * long_len, 0x7fffffffLL);
+    H.mid_split = s.W >= 4 ? (int)std::min<long long>(2 * long_len, H.mid_len) : H.mid_len;
     H.seg_len = 16 * (32 / s.W) * bs;
     H.block_rows = t.block_rows > 0 ? std::min(t.block_rows, kMaxBlockRows) : (s.W >= 16 ? 64 : 128);
     // mid rows: at most nnz / (long_len + 1) rows are longer than long_len; single rows: at most
@@ -260,7 +266,7 @@ HybridLayout hybrid_layout(int m, long long nnz, int n, const Shape& s, const sp
     H.max_parts = (int)std::min<long long>(parts, 0x7fffffffLL);
     size_t off = 0;
     H.off_counts = off;
-    off = align256(off + 4 * sizeof(int));
+    off = align256(off + 5 * sizeof(int));
     H.off_mid = off;
     off = align256(off + (size_t)H.max_mid * sizeof(int));
     H.off_single = off;
@@ -497,6 +503,7 @@ int run_spmm(const Launchers* L, int m, int k, int n, long long nnz, const int* 
         LongRowArgs la{};
         la.long_len = H.long_len;
         la.mid_len = H.mid_len;
+        la.mid_split = H.mid_split;
         la.seg_len = H.seg_len;
         la.block_rows = H.block_rows;
         la.max_mid = H.max_mid;

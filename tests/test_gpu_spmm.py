@@ -509,7 +509,9 @@ def test_host_entry_few_long_rows(gpu_lib):
 @pytest.mark.parametrize("long_row_len", [1, 7, 64, 1000])
 def test_hybrid_integer_rows_across_the_threshold_are_bitwise(gpu_lib, n, long_row_len):
     """Hybrid row split: rows just below, at and above the long-row threshold,
-    rows taken by one lane group and rows of many segments (up to 40,000
+    rows taken by one lane group (at and just above twice the threshold, where
+    they move from the front to the back of the queue, and at and just above
+    four times it, where they leave it), and rows of many segments (up to 40,000
     nonzeros, so with 512-nonzero segments up to 79 partial sums added by the
     row's last warp) on integer data, with blocks of 1, 37, 128 and 256 rows per
     warp: every partial sum is an exact integer, so the result must equal the
@@ -521,6 +523,10 @@ def test_hybrid_integer_rows_across_the_threshold_are_bitwise(gpu_lib, n, long_r
     lens = rng.integers(0, 80, 6000)
     lens[::211] = long_row_len
     lens[1::211] = long_row_len + 1
+    lens[2::211] = 2 * long_row_len
+    lens[3::211] = 2 * long_row_len + 1
+    lens[4::211] = 4 * long_row_len
+    lens[6::211] = 4 * long_row_len + 1
     lens[::997] = 40_000
     lens[5] = 0
     rp, ci, v = csr_arrays(lens, 50_000, 21, int_vals=True)
