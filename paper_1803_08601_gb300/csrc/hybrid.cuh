@@ -24,6 +24,12 @@ namespace spmm {
 constexpr int kMaxRowSegs = 64;
 constexpr int kMaxBlockRows = 256;  // rows per warp of the row-block pass, at most
 
+// Lane groups of 4 or more lanes queue their mid rows in two length classes
+// (mid_split); narrower ones keep one class, and their kernels carry no code
+// for the second.
+template <int W>
+__host__ __device__ constexpr bool split_mid_rows() { return W >= 4; }
+
 __host__ __device__ __forceinline__ int long_row_segments(long long len, int seg_len) {
     const long long s = (len + seg_len - 1) / seg_len;
     return (int)(s < kMaxRowSegs ? s : kMaxRowSegs);
@@ -32,7 +38,6 @@ __host__ __device__ __forceinline__ int long_row_segments(long long len, int seg
 struct LongRowArgs {
     int long_len;     // rows with more nonzeros than this leave the row-block pass
     int mid_len;      // queued rows of at most this many nonzeros are taken by one lane group
-    int mid_split;    // mid rows of at most this many nonzeros fill mid[] from the front, longer from the back
     int seg_len;      // nonzeros per warp segment of a longer row (before the kMaxRowSegs cap)
     int block_rows;   // rows per warp in the row-block pass (1 .. kMaxBlockRows)
     int max_mid;      // capacity of mid[]
@@ -47,6 +52,7 @@ struct LongRowArgs {
     int* arrive;      // [max_parts]: segments of a row finished so far, at the row's first partial slot
     float* partial;   // [max_parts][n]: one partial sum per segment of a row with several segments
     int* status;      // optional device status word
+    int mid_split;    // mid rows of at most this many nonzeros fill mid[] from the front, longer from the back
 };
 
 // ============================================================================ hybrid row split
@@ -105,6 +111,7 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
     __syncwarp();
 
     // each lane takes a run of the block's rows: weights (length of a short row, else 0) and queue counts
+    constexpr bool kSplit = split_mid_rows<W>();
     const int rpl = (nr + 31) / 32;
     const int i0 = min(lane * rpl, nr), i1 = min(i0 + rpl, nr);
     int wsum = 0, nmid = 0, nmid2 = 0, nsingle = 0, nparts = 0;
@@ -113,8 +120,12 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
         if (len <= l.long_len) {
             wsum += len;
         } else if (len <= l.mid_len) {
-            if (len <= l.mid_split) ++nmid;
-            else ++nmid2;
+            if constexpr (kSplit) {
+                if (len <= l.mid_split) ++nmid;
+                else ++nmid2;
+            } else {
+                ++nmid;
+            }
         } else {
             const int ns = long_row_segments(len, l.seg_len);
             if (ns == 1) ++nsingle;
@@ -136,59 +147,113 @@ __global__ void __launch_bounds__(kThreads, block_pass_min_blocks<VEC, W>()) row
         }
         if (lane == 31) s_w[nr] = incl;
     }
-    // queue the longer rows (the slab-0 CTA only): one reservation per queue per warp
-    if (blockIdx.y == 0 && __any_sync(kFullMask, nmid + nmid2 + nsingle + nparts > 0)) {
-        int xm = nmid, xm2 = nmid2, xs = nsingle, xp = nparts;  // inclusive prefixes over the lanes
+    // queue the longer rows (the slab-0 CTA only): one reservation per queue per warp.  The one-class
+    // form is kept verbatim for narrow lane groups: their kernels ran up to 15 % slower on long rows
+    // when compiled from the two-class source, even with the second class folded away.
+    if constexpr (kSplit) {
+        if (blockIdx.y == 0 && __any_sync(kFullMask, nmid + nmid2 + nsingle + nparts > 0)) {
+            int xm = nmid, xm2 = nmid2, xs = nsingle, xp = nparts;  // inclusive prefixes over the lanes
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int ym = __shfl_up_sync(kFullMask, xm, off);
-            const int ym2 = __shfl_up_sync(kFullMask, xm2, off);
-            const int ys = __shfl_up_sync(kFullMask, xs, off);
-            const int yp = __shfl_up_sync(kFullMask, xp, off);
-            if (lane >= off) {
-                xm += ym;
-                xm2 += ym2;
-                xs += ys;
-                xp += yp;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ym = __shfl_up_sync(kFullMask, xm, off);
+                const int ys = __shfl_up_sync(kFullMask, xs, off);
+                const int yp = __shfl_up_sync(kFullMask, xp, off);
+                const int ym2 = __shfl_up_sync(kFullMask, xm2, off);
+                if (lane >= off) {
+                    xm += ym;
+                    xm2 += ym2;
+                    xs += ys;
+                    xp += yp;
+                }
+            }
+            int bm = 0, bm2 = 0, bs = 0, bp = 0;
+            if (lane == 31) {
+                if (xm) bm = atomicAdd(l.counts + 3, xm);
+                if (xm2) bm2 = atomicAdd(l.counts + 4, xm2);
+                if (xs) bs = atomicAdd(l.counts + 0, xs);
+                if (xp) bp = atomicAdd(l.counts + 1, xp);
+            }
+            bm = __shfl_sync(kFullMask, bm, 31) + xm - nmid;
+            bm2 = __shfl_sync(kFullMask, bm2, 31) + xm2 - nmid2;
+            bs = __shfl_sync(kFullMask, bs, 31) + xs - nsingle;
+            bp = __shfl_sync(kFullMask, bp, 31) + xp - nparts;
+            for (int i = i0; i < i1; ++i) {
+                const int len = s_rp[i + 1] - s_rp[i];
+                if (len <= l.long_len) continue;
+                const int row = (int)(r0 + i);
+                if (len <= l.mid_len) {
+                    // the front and the back of mid[] together hold at most max_mid rows for a valid matrix;
+                    // the segment pass checks that they did not meet
+                    const int slot = len <= l.mid_split ? bm++ : l.max_mid - 1 - bm2++;
+                    if (slot >= 0 && slot < l.max_mid) l.mid[slot] = row;
+                    else report(l.status, SPMM_ERR_BAD_CSR);  // more nonzeros than the workspace was sized for
+                    continue;
+                }
+                const int ns = long_row_segments(len, l.seg_len);
+                if (ns == 1) {
+                    if (bs < l.max_singles) l.single[bs] = row;
+                    else report(l.status, SPMM_ERR_BAD_CSR);
+                    ++bs;
+                } else if ((long long)bp + ns <= l.max_parts) {
+                    for (int t = 0; t < ns; ++t) l.multi[bp + t] = make_int2(row, bp);
+                    l.arrive[bp] = 0;
+                    bp += ns;
+                } else {
+                    // the row is left out; its reserved slots that exist are marked empty for the segment pass
+                    for (long long t = bp; t < (long long)bp + ns && t < l.max_parts; ++t) l.multi[t] = make_int2(-1, 0);
+                    report(l.status, SPMM_ERR_BAD_CSR);
+                    bp += ns;
+                }
             }
         }
-        int bm = 0, bm2 = 0, bs = 0, bp = 0;
-        if (lane == 31) {
-            if (xm) bm = atomicAdd(l.counts + 3, xm);
-            if (xm2) bm2 = atomicAdd(l.counts + 4, xm2);
-            if (xs) bs = atomicAdd(l.counts + 0, xs);
-            if (xp) bp = atomicAdd(l.counts + 1, xp);
-        }
-        bm = __shfl_sync(kFullMask, bm, 31) + xm - nmid;
-        bm2 = __shfl_sync(kFullMask, bm2, 31) + xm2 - nmid2;
-        bs = __shfl_sync(kFullMask, bs, 31) + xs - nsingle;
-        bp = __shfl_sync(kFullMask, bp, 31) + xp - nparts;
-        for (int i = i0; i < i1; ++i) {
-            const int len = s_rp[i + 1] - s_rp[i];
-            if (len <= l.long_len) continue;
-            const int row = (int)(r0 + i);
-            if (len <= l.mid_len) {
-                // the front and the back of mid[] together hold at most max_mid rows for a valid matrix;
-                // the segment pass checks that they did not meet
-                const int slot = len <= l.mid_split ? bm++ : l.max_mid - 1 - bm2++;
-                if (slot >= 0 && slot < l.max_mid) l.mid[slot] = row;
-                else report(l.status, SPMM_ERR_BAD_CSR);  // more nonzeros than the workspace was sized for
-                continue;
+    } else {
+        if (blockIdx.y == 0 && __any_sync(kFullMask, nmid + nsingle + nparts > 0)) {
+            int xm = nmid, xs = nsingle, xp = nparts;  // inclusive prefixes over the lanes
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ym = __shfl_up_sync(kFullMask, xm, off);
+                const int ys = __shfl_up_sync(kFullMask, xs, off);
+                const int yp = __shfl_up_sync(kFullMask, xp, off);
+                if (lane >= off) {
+                    xm += ym;
+                    xs += ys;
+                    xp += yp;
+                }
             }
-            const int ns = long_row_segments(len, l.seg_len);
-            if (ns == 1) {
-                if (bs < l.max_singles) l.single[bs] = row;
-                else report(l.status, SPMM_ERR_BAD_CSR);
-                ++bs;
-            } else if ((long long)bp + ns <= l.max_parts) {
-                for (int t = 0; t < ns; ++t) l.multi[bp + t] = make_int2(row, bp);
-                l.arrive[bp] = 0;
-                bp += ns;
-            } else {
-                // the row is left out; its reserved slots that exist are marked empty for the segment pass
-                for (long long t = bp; t < (long long)bp + ns && t < l.max_parts; ++t) l.multi[t] = make_int2(-1, 0);
-                report(l.status, SPMM_ERR_BAD_CSR);
-                bp += ns;
+            int bm = 0, bs = 0, bp = 0;
+            if (lane == 31) {
+                if (xm) bm = atomicAdd(l.counts + 3, xm);
+                if (xs) bs = atomicAdd(l.counts + 0, xs);
+                if (xp) bp = atomicAdd(l.counts + 1, xp);
+            }
+            bm = __shfl_sync(kFullMask, bm, 31) + xm - nmid;
+            bs = __shfl_sync(kFullMask, bs, 31) + xs - nsingle;
+            bp = __shfl_sync(kFullMask, bp, 31) + xp - nparts;
+            for (int i = i0; i < i1; ++i) {
+                const int len = s_rp[i + 1] - s_rp[i];
+                if (len <= l.long_len) continue;
+                const int row = (int)(r0 + i);
+                if (len <= l.mid_len) {
+                    if (bm < l.max_mid) l.mid[bm] = row;
+                    else report(l.status, SPMM_ERR_BAD_CSR);  // more nonzeros than the workspace was sized for
+                    ++bm;
+                    continue;
+                }
+                const int ns = long_row_segments(len, l.seg_len);
+                if (ns == 1) {
+                    if (bs < l.max_singles) l.single[bs] = row;
+                    else report(l.status, SPMM_ERR_BAD_CSR);
+                    ++bs;
+                } else if ((long long)bp + ns <= l.max_parts) {
+                    for (int t = 0; t < ns; ++t) l.multi[bp + t] = make_int2(row, bp);
+                    l.arrive[bp] = 0;
+                    bp += ns;
+                } else {
+                    // the row is left out; its reserved slots that exist are marked empty for the segment pass
+                    for (long long t = bp; t < (long long)bp + ns && t < l.max_parts; ++t) l.multi[t] = make_int2(-1, 0);
+                    report(l.status, SPMM_ERR_BAD_CSR);
+                    bp += ns;
+                }
             }
         }
     }
@@ -346,11 +411,15 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
     // the mid rows, NG to a work item: the longer ones (from the back of mid[]) before the shorter ones
     const int n_multi = min(__ldcg(l.counts + 1), l.max_parts);
     const int n_single = min(__ldcg(l.counts), l.max_singles);
-    int n_mid = min(__ldcg(l.counts + 3), l.max_mid);
-    int n_mid2 = min(__ldcg(l.counts + 4), l.max_mid);
-    if (n_mid + n_mid2 > l.max_mid) {  // the two ends met: not a valid matrix for this workspace
-        if (threadIdx.x == 0 && blockIdx.x == 0) report(l.status, SPMM_ERR_BAD_CSR);
-        n_mid2 = l.max_mid - n_mid;
+    constexpr bool kSplit = split_mid_rows<W>();
+    const int n_mid = min(__ldcg(l.counts + 3), l.max_mid);
+    int n_mid2 = 0;  // stays 0 for narrow lane groups (one class)
+    if constexpr (kSplit) {
+        n_mid2 = min(__ldcg(l.counts + 4), l.max_mid);
+        if (n_mid + n_mid2 > l.max_mid) {  // the two ends met: not a valid matrix for this workspace
+            if (threadIdx.x == 0 && blockIdx.x == 0) report(l.status, SPMM_ERR_BAD_CSR);
+            n_mid2 = l.max_mid - n_mid;
+        }
     }
     const int items2 = (n_mid2 + NG - 1) / NG;  // work items of the longer mid rows
     const int count = n_multi + n_single + items2 + (n_mid + NG - 1) / NG;
@@ -363,16 +432,22 @@ __global__ void __launch_bounds__(kThreads, 3) rowsplit_segment_kernel(RowSplitA
         const int slab = (int)(item / count);
         const int i = (int)(item - (long long)slab * count);
         if (i >= n_multi + n_single) {  // one lane group per mid row
-            const int t = i - n_multi - n_single;
-            int r = -1;
-            if (t < items2) {
-                const int q = t * NG + grp;
-                if (q < n_mid2) r = __ldcg(l.mid + (l.max_mid - 1 - q));
+            if constexpr (kSplit) {
+                const int t = i - n_multi - n_single;
+                int r = -1;
+                if (t < items2) {
+                    const int q = t * NG + grp;
+                    if (q < n_mid2) r = __ldcg(l.mid + (l.max_mid - 1 - q));
+                } else {
+                    const int q = (t - items2) * NG + grp;
+                    if (q < n_mid) r = __ldcg(l.mid + q);
+                }
+                rowsplit_row<TV, TB, TC, VEC, W, SR>(a, (r < 0 || r >= a.m) ? (long long)a.m : (long long)r, slab);
             } else {
-                const int q = (t - items2) * NG + grp;
-                if (q < n_mid) r = __ldcg(l.mid + q);
+                const int q = (i - n_multi - n_single) * NG + grp;
+                const int r = q < n_mid ? __ldcg(l.mid + q) : -1;
+                rowsplit_row<TV, TB, TC, VEC, W, SR>(a, (r < 0 || r >= a.m) ? (long long)a.m : (long long)r, slab);
             }
-            rowsplit_row<TV, TB, TC, VEC, W, SR>(a, (r < 0 || r >= a.m) ? (long long)a.m : (long long)r, slab);
             continue;
         }
         const long long col0 = (long long)slab * (W * VEC) + (long long)sl * VEC;

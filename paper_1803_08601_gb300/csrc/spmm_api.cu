@@ -252,7 +252,7 @@ HybridLayout hybrid_layout(int m, long long nnz, int n, const Shape& s, const sp
     const long long long_len = t.long_row_len > 0 ? t.long_row_len : def_long;
     H.long_len = (int)std::min<long long>(long_len, 0x3fffffffLL);
     H.mid_len = (int)std::min<long long>(4 * long_len, 0x7fffffffLL);
-    H.mid_split = s.W >= 4 ? (int)std::min<long long>(2 * long_len, H.mid_len) : H.mid_len;
+    H.mid_split = s.W >= 4 ? (int)std::min<long long>(2 * long_len, H.mid_len) : H.mid_len;  // split_mid_rows
     H.seg_len = 16 * (32 / s.W) * bs;
     H.block_rows = t.block_rows > 0 ? std::min(t.block_rows, kMaxBlockRows) : (s.W >= 16 ? 64 : 128);
     // mid rows: at most nnz / (long_len + 1) rows are longer than long_len; single rows: at most
