@@ -572,3 +572,32 @@ def test_hybrid_rejects_a_short_workspace(gpu_lib):
     ws = torch.empty(need // 4 // 256 * 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(gpu_lib.SpMMError):
         run(gpu_lib, torch, rp, ci, v, B, "hybrid", workspace=ws)
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_hybrid_reports_an_understated_nonzero_count(gpu_lib, lanes):
+    """The hybrid's queues are sized from the nnz the caller passes.  With a
+    quarter of the true count, the 800 queued rows of 40 and 100 nonzeros
+    overflow the mid queue (capacity nnz / 33 + 1 = 434): with 2-lane groups the
+    row-block pass runs past its end; with 4-lane groups the rows of 40 fill it
+    from the front and those of 100 from the back, the two ends meet inside it,
+    and the segment pass finds that.  Either way the call reports
+    SPMM_ERR_BAD_CSR on the status word; every queue write is bounds-checked."""
+    import torch
+
+    lens = np.array([40, 100, 3] * 400, dtype=np.int64)
+    rp, ci, v = csr_arrays(lens, 5_000, 31)
+    B = gen.normal_matrix(5_000, 32, 32)
+    d_rp, d_ci, d_v, d_B = to_dev(torch, rp, ci, v, B)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gpu_lib.spmm(d_rp, d_ci, d_v, d_B, alg="hybrid", nnz=int(rp[-1]) // 4, status=status,
+                 tuning={"lanes_per_row": lanes})
+    torch.cuda.synchronize()
+    assert int(status.item()) == gpu_lib.ERR_BAD_CSR
+    # with the true count the same call is exact
+    status.zero_()
+    C = gpu_lib.spmm(d_rp, d_ci, d_v, d_B, alg="hybrid", nnz=int(rp[-1]), status=status,
+                     tuning={"lanes_per_row": lanes})
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    check(C.cpu().numpy(), rp, ci, v, B)
