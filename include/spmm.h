@@ -109,7 +109,8 @@ typedef struct {
                                 lane group; a tile holds 256 / lanes_per_row groups     */
     int long_row_len;        /* SPMM_ALG_ROW_SPLIT_HYBRID: rows with more nonzeros than
                                 this leave the row-block pass (queued rows of up to 4x
-                                this are taken by one lane group, longer ones by warp
+                                this are taken by one lane group, with 4 or more lanes
+                                per row those above 2x first; longer ones by warp
                                 segments); 0 selects max(32, lanes per row)            */
     double merge_threshold;  /* heuristic threshold on nnz / m; <= 0 selects 9.35       */
     long long max_row_len;   /* SPMM_ALG_AUTO_GB300: longest row of A when the caller
