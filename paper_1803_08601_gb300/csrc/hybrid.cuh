@@ -16,11 +16,11 @@ namespace spmm {
 // most mid_len is queued in mid[] and later taken by one lane group: rows of at
 // most mid_split nonzeros from the front of mid[], longer ones from its back, so
 // that the segment pass can take the longer ones first and put rows of similar
-// length in one warp's work item.  A longer
-// row is cut into nseg = min(ceil(len / seg_len), kMaxRowSegs) segments of
-// equal length, each taken by a whole warp: a row of one segment is queued in
-// single[]; a row of several reserves nseg consecutive partial slots, and slot
-// p holds its segment p - first in multi[p].
+// length in one warp's work item.  A longer row is cut into
+// nseg = min(ceil(len / seg_len), kMaxRowSegs) segments of equal length, each
+// taken by a whole warp: a row of one segment is queued in single[]; a row of
+// several reserves nseg consecutive partial slots, and slot p holds its segment
+// p - first in multi[p].
 constexpr int kMaxRowSegs = 64;
 constexpr int kMaxBlockRows = 256;  // rows per warp of the row-block pass, at most
 
@@ -84,7 +84,10 @@ struct LongRowArgs {
 //   last.
 
 // Row-block pass.  The segment pass may be scheduled as soon as every CTA has
-// started; it waits for this grid to finish.
+// started; it waits for this grid to finish.  Lane groups of up to 8 lanes run
+// 4 CTAs per SM at 64 registers, with a few bytes of spills for two-vector
+// rows: at 3 CTAs and no spills (72 registers) the pass was 7-15 % slower on
+// GB300, since its warps wait on the gathers and more of them keep more in flight.
 template <int VEC, int W>
 __host__ __device__ constexpr int block_pass_min_blocks() { return W >= 16 ? 3 : 4; }
 
